@@ -1,0 +1,196 @@
+/*
+ * hz.h -- C ABI of the GB300 polarized-traces Helmholtz solver (online phase).
+ *
+ * Problem (paper's Formulation section, Eqs. 1 and 3-7): on an nx*ny*nz grid of
+ * spacing h, solve  (Delta_h + omega^2 m) u = f  with absorbing PML pads obtained
+ * by complex coordinate stretching d/dx -> beta(x) d/dx, beta = 1/(1 + i sigma/omega),
+ * sigma quadratic in the pad (Eq. 5).  The discrete operator is used in its
+ * complex-symmetric form A = S (Delta_h^stretched + omega^2 m), S = s_x s_y s_z,
+ * s = 1/beta, and the system solved is  A u = S f.
+ *
+ * Method (SIE and polarized-traces sections, Algorithms 1-9): the domain is cut
+ * into n_layers slabs along z, each padded with its own PML at internal faces;
+ * every slab's local operator is factored once (Algorithm 1) by a multifrontal
+ * nested-dissection LDL^T on the GPU; a solve (Algorithm 2) runs local solves,
+ * forms the polarized trace right-hand side, runs GMRES on P M_pol (Eqs. 14-16)
+ * whose every matrix-vector product is a set of multi-RHS local solves, and
+ * rebuilds the volume with the Green's representation formula.
+ *
+ * Conventions for every entry point:
+ *  - Grids are stored z-slowest, x-fastest: index (z*ny + y)*nx + x.
+ *  - Complex arrays are interleaved (re, im) pairs of double (C99 double _Complex
+ *    layout); a "complex array of length n" is 2n doubles.
+ *  - Pointers documented "device" must be CUDA device (or managed) memory of the
+ *    current device; "host" pointers are ordinary host memory (pinned memory is
+ *    faster for the copies but not required).
+ *  - Every call returns a status and never aborts, traps or exits; on failure
+ *    hz_last_error() returns a one-line reason.  The handle owns every buffer it
+ *    allocates; the caller owns every buffer it passes in.
+ *  - All work is queued on the stream given to hz_create (0 = legacy default
+ *    stream); calls are synchronous with respect to the host on return unless
+ *    stated otherwise.  A handle must not be used from two host threads at once.
+ */
+#ifndef HZ_H
+#define HZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HZ_OK = 0,
+    HZ_ERR_ARG = 1,            /* invalid argument (sizes, null pointers, omega <= 0, ...) */
+    HZ_ERR_OOM = 2,            /* device allocation failed */
+    HZ_ERR_ADMISSION = 3,      /* request does not fit in the free device memory */
+    HZ_ERR_STATE = 4,          /* call out of order (e.g. solve before factor) */
+    HZ_ERR_NONFINITE = 5,      /* NaN/Inf in m, rhs or a result */
+    HZ_ERR_PIVOT = 6,          /* a pivot of the unpivoted LDL^T was tiny or non-finite */
+    HZ_ERR_NO_CONVERGENCE = 7, /* GMRES / refinement hit its iteration cap; u and info still written */
+    HZ_ERR_TIMEOUT = 8,        /* a bounded device-side wait gave up */
+    HZ_ERR_CUDA = 9            /* a CUDA runtime call failed */
+} hz_status;
+
+typedef enum {
+    HZ_PREC_FP64 = 0,  /* complex128 factors and local solves, FP64 GMRES */
+    HZ_PREC_MIXED = 1  /* complex64 factors and local solves (FP64 pivot blocks), FP64 GMRES
+                          on the traces, FP64 volume residual + defect correction */
+} hz_precision;
+
+typedef struct { int32_t nx, ny, nz; double h; } hz_grid;
+
+/* npml: global pad thickness in nodes on every face (sigma measured from the first
+ * physical node, delta = npml*h); C: profile strength of Eq. 5; npml_local: pad
+ * thickness added at internal layer interfaces (<0 means npml). */
+typedef struct { int32_t npml; double C; int32_t npml_local; } hz_pml;
+
+typedef struct {
+    double gmres_tol;    /* stop when ||P(f - M u)|| <= tol ||P f|| per column (default 1e-10 FP64, 1e-7 mixed) */
+    int32_t restart;     /* Krylov dimension before restart (default 20) */
+    int32_t max_iter;    /* total GMRES iterations cap (default 100) */
+    double refine_tol;   /* mixed mode: stop refining when ||S f - A u|| <= refine_tol ||S f|| (default 1e-9) */
+    int32_t max_refine;  /* mixed mode: maximum defect-correction passes (default 3) */
+} hz_solve_opts;
+
+typedef struct {
+    int32_t iters;         /* GMRES iterations of the last pass */
+    int32_t refinements;   /* defect-correction passes done (mixed mode) */
+    double trace_relres;   /* final preconditioned relative residual estimate of GMRES */
+    double volume_relres;  /* ||S f - A u|| / ||S f|| in FP64 (computed when refining or requested) */
+    float ms_total;        /* device time of the whole call for this batch, milliseconds */
+} hz_solve_info;
+
+typedef struct hz_handle hz_handle;
+
+/* Fills *opts with the defaults listed above for the given precision. */
+void hz_default_opts(hz_precision prec, hz_solve_opts* opts);
+
+/*
+ * hz_create -- set up a problem (layered decomposition of the Formulation section,
+ * Fig. 1 and Eq. 6; symbolic nested dissection of every distinct slab shape).
+ *   grid      grid sizes (each >= 3) and spacing h > 0
+ *   m         squared slowness, real, nz*ny*nx doubles, host memory; copied
+ *   omega     angular frequency > 0
+ *   pml       PML parameters (see hz_pml)
+ *   n_layers  number of slabs L, 1 <= L <= number of physical z planes
+ *   prec      HZ_PREC_FP64 or HZ_PREC_MIXED
+ *   stream    cudaStream_t to queue work on (0 for the default stream)
+ *   out       receives the new handle (NULL on failure)
+ * Errors: HZ_ERR_ARG, HZ_ERR_NONFINITE (m), HZ_ERR_OOM, HZ_ERR_CUDA.
+ */
+hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz_pml* pml,
+                    int32_t n_layers, hz_precision prec, void* stream, hz_handle** out);
+
+/*
+ * hz_factor -- offline phase (Algorithm 1): assemble and factor every layer's
+ * local operator H^l = L D L^T (complex symmetric, unpivoted, nested dissection,
+ * FP64 diagonal pivot blocks), keeping the factors resident in device memory.
+ * Errors: HZ_ERR_OOM, HZ_ERR_PIVOT, HZ_ERR_CUDA.
+ */
+hz_status hz_factor(hz_handle* h);
+
+/*
+ * hz_solve -- online phase (Algorithm 2) for R right-hand sides.
+ *   rhs   device, complex array of R*nz*ny*nx: f for each right-hand side
+ *   R     number of right-hand sides, >= 1
+ *   u     device, complex array of R*nz*ny*nx, caller-owned, receives u
+ *   opts  NULL for the defaults
+ *   info  NULL or array of R entries, one per right-hand side (iters etc. of its column)
+ * Errors: HZ_ERR_STATE (not factored), HZ_ERR_ARG, HZ_ERR_ADMISSION (workspace for R
+ * does not fit), HZ_ERR_NONFINITE, HZ_ERR_NO_CONVERGENCE (u and info still written).
+ */
+hz_status hz_solve(hz_handle* h, const double* rhs, int32_t R, double* u,
+                   const hz_solve_opts* opts, hz_solve_info* info);
+
+/*
+ * hz_solve_host -- as hz_solve with HOST rhs and u: copies rhs to the device, solves,
+ * copies u back (end-to-end entry point).  Same errors as hz_solve.
+ */
+hz_status hz_solve_host(hz_handle* h, const double* rhs_host, int32_t R, double* u_host,
+                        const hz_solve_opts* opts, hz_solve_info* info);
+
+/* hz_destroy -- frees every device and host buffer of the handle (NULL is allowed). */
+hz_status hz_destroy(hz_handle* h);
+
+/* One-line description of the last failure on this handle ("" if none); the string
+ * stays valid until the next call on the handle.  h may be NULL (reports failures of
+ * hz_create). */
+const char* hz_last_error(const hz_handle* h);
+
+/* ------------------------------------------------------------------------------------
+ * Introspection and stage-level entry points.  Each runs one step of the online path
+ * on the device so that it can be checked on its own; none is needed for a solve.
+ * ------------------------------------------------------------------------------------ */
+
+/* Layer geometry: owned global planes [lo, hi] and extended local grid [zlo, zhi]
+ * of layer ell (0-based). */
+hz_status hz_layer_info(const hz_handle* h, int32_t ell, int32_t* lo, int32_t* hi,
+                        int32_t* zlo, int32_t* zhi);
+
+/* Statistics of the symbolic/numeric factorization: number of tree nodes, stored
+ * factor entries (padded tiles, summed over layers), factorization flops (real),
+ * front workspace bytes, and the time hz_factor took in milliseconds. */
+hz_status hz_factor_stats(const hz_handle* h, int64_t* nodes, int64_t* factor_entries,
+                          double* factor_flops, int64_t* workspace_bytes, float* factor_ms);
+
+/* Bytes of packed factors streamed by one forward+backward substitution of layer ell
+ * (each factor tile read once forward, once backward), and its real flop count per
+ * right-hand-side column. */
+hz_status hz_layer_solve_cost(const hz_handle* h, int32_t ell, double* bytes, double* flops_per_col);
+
+/*
+ * Local solve (Algorithm 2, "solve local problems"): w = (H^ell)^{-1} g for ncols
+ * columns on layer ell's extended local grid of nzl = zhi-zlo+1 planes.
+ *   g, w  device, complex arrays [ncols][nzl][ny][nx] (natural local order)
+ */
+hz_status hz_layer_solve(hz_handle* h, int32_t ell, const double* g, int32_t ncols, double* w);
+
+/*
+ * Polarized right-hand side (Algorithm 2, local solves + forming the trace rhs):
+ *   rhs   device complex [R][nz][ny][nx], f (scaled by S inside)
+ *   fpol  device complex [R][2][K][2][ny][nx]: (down, up) x interface j x (P_j, Q_j) planes
+ * K = n_layers - 1.
+ */
+hz_status hz_polarized_rhs(hz_handle* h, const double* rhs, int32_t R, double* fpol);
+
+/* y = M_pol x (appendix, Application Polarized: Algorithms 6-9), x and y device
+ * complex [R][2][K][2][ny][nx]. */
+hz_status hz_apply_mpol(hz_handle* h, const double* x, int32_t R, double* y);
+
+/* y = P x, the Gauss-Seidel preconditioner of Eq. 16 (Algorithms 4-6), same layout. */
+hz_status hz_apply_precond(hz_handle* h, const double* x, int32_t R, double* y);
+
+/* Reconstruction (Algorithm 2, inner solves): u from f and the traces t = u_down + u_up,
+ * t device complex [R][K][2][ny][nx]; u device complex [R][nz][ny][nx]. */
+hz_status hz_reconstruct(hz_handle* h, const double* rhs, const double* t, int32_t R, double* u);
+
+/* FP64 volume residual r = S f - A u (7-point stencil of the global operator) and its
+ * per-column relative norms ||r|| / ||S f||; r may be NULL. */
+hz_status hz_volume_residual(hz_handle* h, const double* rhs, const double* u, int32_t R,
+                             double* r, double* relres_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HZ_H */

@@ -1,0 +1,71 @@
+// Solver context shared by the translation units (the object behind hz_handle).
+#pragma once
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "hz_internal.cuh"
+
+namespace hz {
+
+__device__ __host__ inline int cdiv_dev(int a, int b) { return (a + b - 1) / b; }
+
+// FP64 inputs of the stencil coefficients of one layer's local operator.
+struct LayerCoef {
+    const double2* sx_n;   // s_x at nodes (nx)
+    const double2* isx_h;  // 1/s_x at half nodes (nx+1), index i <-> i - 1/2
+    const double2* sy_n;
+    const double2* isy_h;
+    const double2* sz_n;   // local z profile (nzl)
+    const double2* isz_h;  // (nzl+1)
+    const double* m;       // local m (nzl*ny*nx)
+    int nx, ny;
+    double omega2, inv_h2;
+};
+
+// A set of layers solved together (one job per layer) with its per-level task lists.
+struct Batch {
+    std::vector<int> layers;
+    int H = 0;
+    std::vector<long long> own_off, own_n, upd_off, upd_n;  // per level, into d_tasks
+    Task* d_tasks = nullptr;
+    void* d_jobs = nullptr;  // JobDev<C>[njobs]
+};
+
+struct Ctx {
+    // problem
+    int nx = 0, ny = 0, nz = 0;
+    double h = 1.0, omega = 0.0, C = 0.0;
+    int npml = 0, npml_loc = 0, L = 1, K = 0;
+    hz_precision prec = HZ_PREC_FP64;
+    cudaStream_t stream = 0;
+    long long P = 0;     // plane size nx*ny
+    long long ntr = 0;   // polarized trace vector length per RHS: 2*K*2*P
+    // decomposition and symbolic data
+    std::vector<Shape> shapes;
+    std::vector<Layer> layers;
+    LayerCoef* d_coefs = nullptr;
+    // global FP64 profiles and medium (volume residual, source scaling, interface weights)
+    double2 *d_sx_n = nullptr, *d_isx_h = nullptr, *d_sy_n = nullptr, *d_isy_h = nullptr;
+    double2 *d_sz_n = nullptr, *d_isz_h = nullptr;
+    double* d_m = nullptr;
+    int* d_flag = nullptr;   // device error flags: [0] tiny pivot
+    bool factored = false;
+    long long workspace_bytes = 0;
+    float factor_ms = 0.f;
+    // solve workspaces
+    int slot_cap = 0;        // columns per layer slot
+    std::vector<void*> slot_acc, slot_x;   // per layer, N_layer * slot_cap complex
+    std::map<std::string, Batch> batches;
+    std::string last_error;
+};
+
+template <class C> void factor_layers(Ctx& ctx);
+
+}  // namespace hz
+
+struct hz_handle {
+    hz::Ctx ctx;
+};

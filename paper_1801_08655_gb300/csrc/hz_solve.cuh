@@ -1,0 +1,35 @@
+// Declarations of the batched local-solve driver (solve.cu) and the online-phase
+// operators (polarized.cu).
+#pragma once
+
+#include "hz_ctx.cuh"
+
+namespace hz {
+
+int chunk_cols(bool is_double, int ncols);
+int padded_ldc(bool is_double, int ncols);
+
+// Job set with per-level task lists, cached by layer list.
+template <class C> Batch& get_batch(Ctx& ctx, const std::vector<int>& layers);
+void free_batches(Ctx& ctx);
+
+// Forward/backward substitution for every job of the batch on ncols columns of the
+// layers' slot vectors (acc holds the right-hand side in elimination order on entry and
+// is clobbered; x receives the solution).
+template <class C> void substitute(const Batch& b, int ncols, cudaStream_t st);
+
+// Online operators on polarized trace vectors [R][2][K][2][P] (complex128, device).
+template <class C> void op_polarized_rhs(Ctx& ctx, const double2* g, bool scale, int R, double2* fpol);
+template <class C> void op_apply_mpol(Ctx& ctx, const double2* x, int R, double2* y);
+template <class C> void op_apply_precond(Ctx& ctx, const double2* x, int R, double2* y, double2* tmp);
+template <class C> void op_reconstruct(Ctx& ctx, const double2* g, bool scale, const double2* t, int R,
+                                       double2* u, bool accumulate);
+template <class C> void op_layer_solve(Ctx& ctx, int ell, const double2* g, int ncols, double2* w);
+void op_volume_residual(Ctx& ctx, const double2* f, bool scale, const double2* u, int R, double2* r,
+                        double* norms /* device, 2R: ||r||^2, ||g||^2 */);
+
+struct GmresOut { int iters; double relres; };
+template <class C> void gmres_solve(Ctx& ctx, const double2* g, bool scale, int R, double2* u,
+                                    const hz_solve_opts& o, hz_solve_info* info);
+
+}  // namespace hz

@@ -1,0 +1,939 @@
+// Online phase of the method of polarized traces on the GPU.
+//
+// Indices are 0-based: layers l = 0..L-1, interfaces j = 0..K-1 (K = L-1); interface j
+// carries the plane pair (P_j, Q_j) = (last owned plane of layer j, first owned plane of
+// layer j+1).  A polarized trace vector per right-hand side is stored as
+// [2 (down, up)][K][2 (P, Q)][ny][nx] in complex128, right-hand sides outermost.
+//
+// Interface sources (the Dirac deltas of the Formulation section, weights taken from the
+// assembled matrix so that the discrete Green's representation formula is exact):
+//   S_top(t_{l-1}) on layer l:  plane Q_{l-1} += -c t(P_{l-1});  pad plane P_{l-1} += +c t(Q_{l-1})
+//   S_bot(t_l)     on layer l:  plane P_l     += -c t(Q_l);      pad plane Q_l     += +c t(P_l)
+// with c = s_x s_y / h^2 the z-coupling across a physical half plane.
+// Read-outs: "bottom" of layer l = planes (P_l, Q_l), "top" of layer l = (P_{l-1}, Q_{l-1}).
+//
+// Blocks of the polarized matrix (appendix, Algorithms 6-9) and the preconditioner of
+// Eq. 16 (Algorithms 4-6) are built from one batched local solve per layer with the
+// four source blocks stacked as columns (M_pol), or one layer at a time (sweeps).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "hz_internal.cuh"
+#include "hz_ctx.cuh"
+#include "hz_solve.cuh"
+
+namespace hz {
+
+namespace {
+
+template <class C> __device__ inline void atomic_addc(C* p, double2 v);
+template <> __device__ inline void atomic_addc<float2>(float2* p, double2 v) {
+    atomicAdd(&p->x, (float)v.x);
+    atomicAdd(&p->y, (float)v.y);
+}
+template <> __device__ inline void atomic_addc<double2>(double2* p, double2 v) {
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+}
+
+template <class C> struct Inject {
+    C* acc;
+    const int* pos;
+    const double2* src;      // trace pair base for r = 0; plane P at +0, Q at +plane
+    long long rstride;       // between right-hand sides in src
+    int ldc, col0;
+    int zl_m, off_m;         // local plane receiving -c * src[off_m + cell]
+    int zl_p, off_p;         // local plane receiving +c * src[off_p + cell]
+};
+
+template <class C>
+__global__ void k_inject(const Inject<C>* inj, const double2* sx, const double2* sy, double inv_h2,
+                         int nx, int ny) {
+    const Inject<C> q = inj[blockIdx.z];
+    const int P = nx * ny;
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (cell >= P) return;
+    const int x = cell % nx, y = cell / nx;
+    const double2 c = cscale(cmul(sx[x], sy[y]), inv_h2);
+    const double2* s = q.src + (long long)r * q.rstride;
+    const double2 vm = cneg(cmul(c, s[q.off_m + cell]));
+    const double2 vp = cmul(c, s[q.off_p + cell]);
+    atomic_addc(q.acc + (long long)q.pos[q.zl_m * P + cell] * q.ldc + q.col0 + r, vm);
+    atomic_addc(q.acc + (long long)q.pos[q.zl_p * P + cell] * q.ldc + q.col0 + r, vp);
+}
+
+template <class C> struct Extract {
+    const C* x;
+    const int* pos;
+    double2* dst;            // destination plane for r = 0
+    long long rstride;
+    int ldc, zl, nblk;
+    int cols[4];
+    double sign;
+};
+
+template <class C>
+__global__ void k_extract(const Extract<C>* ex, int P) {
+    const Extract<C> q = ex[blockIdx.z];
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (cell >= P) return;
+    const C* xr = q.x + (long long)q.pos[q.zl * P + cell] * q.ldc + r;
+    double2 s = make_double2(0.0, 0.0);
+    for (int b = 0; b < q.nblk; ++b) s = cadd(s, to_d(xr[q.cols[b]]));
+    double2* d = q.dst + (long long)r * q.rstride + cell;
+    *d = cadd(*d, cscale(s, q.sign));
+}
+
+template <class C> struct VolIO {
+    C* vec;                  // acc (sources) or x (read-out)
+    const int* pos;
+    int ldc, col0, lo, hi, zlo;
+};
+
+// acc[pos(cell)][col0 + r] = S * g[r][z][cell] over the layer's owned planes.
+template <class C>
+__global__ void k_volume_source(const VolIO<C>* io, const double2* g, int R, long long N3, int nx, int ny,
+                                const double2* sx, const double2* sy, const double2* sz, int scale) {
+    const VolIO<C> q = io[blockIdx.z];
+    const int P = nx * ny;
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    const int z = q.lo + blockIdx.y;
+    if (cell >= P || z > q.hi) return;
+    double2 S = make_double2(1.0, 0.0);
+    if (scale) S = cmul(cmul(sx[cell % nx], sy[cell / nx]), sz[z]);
+    C* dst = q.vec + (long long)q.pos[(z - q.zlo) * P + cell] * q.ldc + q.col0;
+    const double2* src = g + (long long)z * P + cell;
+    for (int r = 0; r < R; ++r) dst[r] = from_d<C>(cmul(S, src[(long long)r * N3]));
+}
+
+// u[r][z][cell] (+)= x[pos(cell)][col0 + r] over the owned planes.
+template <class C>
+__global__ void k_volume_out(const VolIO<C>* io, double2* u, int R, long long N3, int P, int accumulate) {
+    const VolIO<C> q = io[blockIdx.z];
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    const int z = q.lo + blockIdx.y;
+    if (cell >= P || z > q.hi) return;
+    const C* src = q.vec + (long long)q.pos[(z - q.zlo) * P + cell] * q.ldc + q.col0;
+    double2* dst = u + (long long)z * P + cell;
+    for (int r = 0; r < R; ++r) {
+        double2 v = to_d(src[r]);
+        if (accumulate) v = cadd(v, dst[(long long)r * N3]);
+        dst[(long long)r * N3] = v;
+    }
+}
+
+// Natural-order local vectors <-> elimination-order slot (stage entry point).
+template <class C>
+__global__ void k_gather_local(C* acc, const int* pos, int ldc, const double2* g, long long Nl, int ncols) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y;
+    if (i >= Nl) return;
+    acc[(long long)pos[i] * ldc + c] = from_d<C>(g[(long long)c * Nl + i]);
+}
+template <class C>
+__global__ void k_scatter_local(const C* x, const int* pos, int ldc, double2* w, long long Nl, int ncols) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y;
+    if (i >= Nl) return;
+    w[(long long)c * Nl + i] = to_d(x[(long long)pos[i] * ldc + c]);
+}
+
+// y = a * x (+ b * z restricted to one plane of each pair) over trace pairs.
+// Pair j of a vector with pair stride 2P: planes [2P j, 2P j + 2P).
+__global__ void k_pairs_axpy(double2* y, long long ystride, const double2* x, long long xstride, double a,
+                             const double2* z, long long zstride, double b, int zplane, int npairs, int P) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int r = blockIdx.y;
+    long long n = (long long)npairs * 2 * P;
+    if (i >= n) return;
+    double2 v = cscale(x[(long long)r * xstride + i], a);
+    if (z != nullptr) {
+        int pl = (int)((i / P) % 2);
+        if (pl == zplane) v = cadd(v, cscale(z[(long long)r * zstride + i], b));
+    }
+    y[(long long)r * ystride + i] = v;
+}
+
+// ------------------------------------------------------------------------------------------
+// FP64 volume residual r = g - A u, g = S f (scale) or f, with per-column norms
+// ------------------------------------------------------------------------------------------
+__global__ void k_residual(const double2* f, const double2* u, double2* rout, double* norms, int scale,
+                           int nx, int ny, int nz, const double2* sxn, const double2* isxh,
+                           const double2* syn, const double2* isyh, const double2* szn,
+                           const double2* iszh, const double* m, double omega2, double inv_h2) {
+    const long long N3 = (long long)nx * ny * nz;
+    const int r = blockIdx.y;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double rr = 0.0, gg = 0.0;
+    if (i < N3) {
+        int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+        const double2* ur = u + (long long)r * N3;
+        double2 sx = sxn[x], sy = syn[y], sz = szn[z];
+        double2 syz = cmul(sy, sz), sxz = cmul(sx, sz), sxy = cmul(sx, sy);
+        double2 c1 = cscale(cmul(syz, isxh[x]), inv_h2), c2 = cscale(cmul(syz, isxh[x + 1]), inv_h2);
+        double2 c3 = cscale(cmul(sxz, isyh[y]), inv_h2), c4 = cscale(cmul(sxz, isyh[y + 1]), inv_h2);
+        double2 c5 = cscale(cmul(sxy, iszh[z]), inv_h2), c6 = cscale(cmul(sxy, iszh[z + 1]), inv_h2);
+        double2 dg = cscale(cmul(sxy, sz), omega2 * m[i]);
+        dg = csub(dg, cadd(cadd(cadd(c1, c2), cadd(c3, c4)), cadd(c5, c6)));
+        double2 au = cmul(dg, ur[i]);
+        if (x > 0) au = cadd(au, cmul(c1, ur[i - 1]));
+        if (x < nx - 1) au = cadd(au, cmul(c2, ur[i + 1]));
+        if (y > 0) au = cadd(au, cmul(c3, ur[i - nx]));
+        if (y < ny - 1) au = cadd(au, cmul(c4, ur[i + nx]));
+        long long pl = (long long)nx * ny;
+        if (z > 0) au = cadd(au, cmul(c5, ur[i - pl]));
+        if (z < nz - 1) au = cadd(au, cmul(c6, ur[i + pl]));
+        double2 g = f[(long long)r * N3 + i];
+        if (scale) g = cmul(cmul(sxy, sz), g);
+        double2 res = csub(g, au);
+        if (rout) rout[(long long)r * N3 + i] = res;
+        rr = res.x * res.x + res.y * res.y;
+        gg = g.x * g.x + g.y * g.y;
+    }
+    // block reduction
+    for (int o = 16; o > 0; o >>= 1) {
+        rr += __shfl_down_sync(0xffffffffu, rr, o);
+        gg += __shfl_down_sync(0xffffffffu, gg, o);
+    }
+    __shared__ double sr[32], sg[32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { sr[w] = rr; sg[w] = gg; }
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        rr = lane < nw ? sr[lane] : 0.0;
+        gg = lane < nw ? sg[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            rr += __shfl_down_sync(0xffffffffu, rr, o);
+            gg += __shfl_down_sync(0xffffffffu, gg, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&norms[2 * r], rr);
+            atomicAdd(&norms[2 * r + 1], gg);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// batched FP64 GMRES kernels: one Krylov space per right-hand-side column
+// ------------------------------------------------------------------------------------------
+__device__ inline double2 block_sum2(double2 v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    }
+    __shared__ double2 sh[32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double2 s = make_double2(0.0, 0.0);
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        s = lane < nw ? sh[lane] : make_double2(0.0, 0.0);
+        for (int o = 16; o > 0; o >>= 1) {
+            s.x += __shfl_down_sync(0xffffffffu, s.x, o);
+            s.y += __shfl_down_sync(0xffffffffu, s.y, o);
+        }
+    }
+    return s;  // valid in thread 0
+}
+
+// dots[r*ld + i] += <V_i[r], w[r]> (conjugated first argument), i < nv
+__global__ void k_mdot(const double2* V, long long vstride, const double2* w, long long n, int nv,
+                       double2* dots, int ld) {
+    const int r = blockIdx.y;
+    const double2* wr = w + (long long)r * n;
+    for (int i = 0; i < nv; ++i) {
+        const double2* vr = V + (long long)i * vstride + (long long)r * n;
+        double2 s = make_double2(0.0, 0.0);
+        for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+             e += (long long)gridDim.x * blockDim.x) {
+            double2 a = vr[e], b = wr[e];
+            s.x += a.x * b.x + a.y * b.y;
+            s.y += a.x * b.y - a.y * b.x;
+        }
+        s = block_sum2(s);
+        if (threadIdx.x == 0) {
+            atomicAdd(&dots[(long long)r * ld + i].x, s.x);
+            atomicAdd(&dots[(long long)r * ld + i].y, s.y);
+        }
+    }
+}
+
+// w[r] -= sum_i h[r*ld + i] V_i[r]
+__global__ void k_maxpy(const double2* V, long long vstride, double2* w, long long n, int nv,
+                        const double2* h, int ld) {
+    const int r = blockIdx.y;
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double2 acc = w[(long long)r * n + e];
+    for (int i = 0; i < nv; ++i) acc = csub(acc, cmul(h[(long long)r * ld + i], V[(long long)i * vstride + (long long)r * n + e]));
+    w[(long long)r * n + e] = acc;
+}
+
+// x[r] += sum_i y[r*ld + i] V_i[r]
+__global__ void k_maxpy_plus(const double2* V, long long vstride, double2* x, long long n, int nv,
+                             const double2* y, int ld) {
+    const int r = blockIdx.y;
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double2 acc = x[(long long)r * n + e];
+    for (int i = 0; i < nv; ++i) acc = cadd(acc, cmul(y[(long long)r * ld + i], V[(long long)i * vstride + (long long)r * n + e]));
+    x[(long long)r * n + e] = acc;
+}
+
+__global__ void k_nrm2(const double2* w, long long n, double* out) {
+    const int r = blockIdx.y;
+    double s = 0.0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        double2 a = w[(long long)r * n + e];
+        s += a.x * a.x + a.y * a.y;
+    }
+    double2 t = block_sum2(make_double2(s, 0.0));
+    if (threadIdx.x == 0) atomicAdd(&out[r], t.x);
+}
+
+__global__ void k_scale_vec(double2* dst, const double2* src, long long n, const double* scale) {
+    const int r = blockIdx.y;
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    dst[(long long)r * n + e] = cscale(src[(long long)r * n + e], scale[r]);
+}
+
+// y[r] = a x[r] + b z[r] over len elements per column (strided per column)
+__global__ void k_lincomb(double2* y, long long ys, double a, const double2* x, long long xs, double b,
+                          const double2* z, long long zs, long long len) {
+    const int r = blockIdx.y;
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= len) return;
+    double2 v = cscale(x[(long long)r * xs + e], a);
+    if (z) v = cadd(v, cscale(z[(long long)r * zs + e], b));
+    y[(long long)r * ys + e] = v;
+}
+
+// dots[r*(m+1) + i] += y[r*m + i], i < nv
+__global__ void k_accum_dots(double2* dots, const double2* y, int R, int m, int nv) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= R * nv) return;
+    int r = q / nv, i = q % nv;
+    dots[(long long)r * (m + 1) + i] = cadd(dots[(long long)r * (m + 1) + i], y[(long long)r * m + i]);
+}
+
+struct GmresState {
+    double2* H;      // [R][(m+1)*m], H[i + j*(m+1)]
+    double2* cs_sn;  // [R][m] pairs: (c, 0) and s stored as two arrays
+    double2* sn;
+    double2* g;      // [R][m+1]
+    double2* dots;   // [R][m+1] scratch (sum of both CGS passes)
+    double* nrm;     // [R]
+    double* invb;    // [R] 1/beta used to normalise the next basis vector (0 = frozen)
+    double* resid;   // [R] |g_{j+1}|
+    int* active;     // [R]
+    int* kused;      // [R] basis vectors used by each column in this cycle
+    double2* y;      // [R][m]
+};
+
+// start of a cycle: beta = sqrt(nrm), g = (beta, 0, ...), invb = 1/beta
+__global__ void k_gmres_start(GmresState s, int R, int m, double tiny) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    double b = sqrt(s.nrm[r]);
+    for (int i = 0; i <= m; ++i) s.g[(long long)r * (m + 1) + i] = make_double2(0.0, 0.0);
+    s.g[(long long)r * (m + 1)] = make_double2(b, 0.0);
+    s.resid[r] = b;
+    s.kused[r] = 0;
+    bool act = s.active[r] && b > tiny;
+    s.active[r] = act;
+    s.invb[r] = act ? 1.0 / b : 0.0;
+}
+
+// column j of the Hessenberg matrix: h(0..j) from dots, h(j+1) = ||w||; Givens update
+__global__ void k_gmres_arnoldi(GmresState s, int R, int m, int j, double tol_abs_scale, const double* b0,
+                                double tol, double tiny) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    if (!s.active[r]) { s.invb[r] = 0.0; return; }
+    double2* H = s.H + (long long)r * (m + 1) * m;
+    double2* cs = s.cs_sn + (long long)r * m;
+    double2* sn = s.sn + (long long)r * m;
+    double2* g = s.g + (long long)r * (m + 1);
+    const double2* d = s.dots + (long long)r * (m + 1);
+    for (int i = 0; i <= j; ++i) H[i + j * (m + 1)] = d[i];
+    double beta = sqrt(s.nrm[r]);
+    H[j + 1 + j * (m + 1)] = make_double2(beta, 0.0);
+    // previous rotations
+    for (int i = 0; i < j; ++i) {
+        double2 a = H[i + j * (m + 1)], bb = H[i + 1 + j * (m + 1)];
+        double c = cs[i].x;
+        double2 sv = sn[i];
+        double2 na = cadd(cscale(a, c), cmul(sv, bb));
+        double2 nb = csub(cscale(bb, c), cmul(make_double2(sv.x, -sv.y), a));
+        H[i + j * (m + 1)] = na;
+        H[i + 1 + j * (m + 1)] = nb;
+    }
+    double2 h1 = H[j + j * (m + 1)];
+    double2 h2 = H[j + 1 + j * (m + 1)];
+    double a1 = sqrt(h1.x * h1.x + h1.y * h1.y), a2 = sqrt(h2.x * h2.x + h2.y * h2.y);
+    double rho = sqrt(a1 * a1 + a2 * a2);
+    double c;
+    double2 sv;
+    if (rho == 0.0) { c = 1.0; sv = make_double2(0.0, 0.0); }
+    else if (a1 == 0.0) { c = 0.0; sv = make_double2(h2.x / a2, -h2.y / a2); }
+    else {
+        c = a1 / rho;
+        double2 ph = make_double2(h1.x / a1, h1.y / a1);
+        sv = cscale(cmul(ph, make_double2(h2.x, -h2.y)), 1.0 / rho);
+    }
+    cs[j] = make_double2(c, 0.0);
+    sn[j] = sv;
+    H[j + j * (m + 1)] = cadd(cscale(h1, c), cmul(sv, h2));
+    H[j + 1 + j * (m + 1)] = make_double2(0.0, 0.0);
+    double2 gj = g[j];
+    g[j] = cscale(gj, c);
+    g[j + 1] = cneg(cmul(make_double2(sv.x, -sv.y), gj));
+    double res = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y);
+    s.resid[r] = res;
+    s.kused[r] = j + 1;
+    if (res <= tol * sqrt(b0[r]) || beta <= tiny) {
+        s.active[r] = 0;
+        s.invb[r] = 0.0;
+    } else {
+        s.invb[r] = 1.0 / beta;
+    }
+    (void)tol_abs_scale;
+}
+
+// back substitution H(0:k,0:k) y = g(0:k) per column
+__global__ void k_gmres_lsq(GmresState s, int R, int m) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const double2* H = s.H + (long long)r * (m + 1) * m;
+    const double2* g = s.g + (long long)r * (m + 1);
+    double2* y = s.y + (long long)r * m;
+    int k = s.kused[r];
+    for (int i = 0; i < m; ++i) y[i] = make_double2(0.0, 0.0);
+    for (int i = k - 1; i >= 0; --i) {
+        double2 v = g[i];
+        for (int q = i + 1; q < k; ++q) v = csub(v, cmul(H[i + q * (m + 1)], y[q]));
+        y[i] = cmul(v, crecip(H[i + i * (m + 1)]));
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// host-side helpers
+// ------------------------------------------------------------------------------------------
+template <class T> T* upload(const std::vector<T>& v, cudaStream_t st, void*& holder) {
+    T* d = nullptr;
+    HZ_CUDA(cudaMallocAsync((void**)&d, std::max<size_t>(1, v.size()) * sizeof(T), st));
+    if (!v.empty()) HZ_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    holder = d;
+    return d;
+}
+
+struct Scratch {
+    std::vector<void*> ptrs;
+    cudaStream_t st;
+    explicit Scratch(cudaStream_t s) : st(s) {}
+    ~Scratch() { for (void* p : ptrs) cudaFreeAsync(p, st); }
+    template <class T> T* up(const std::vector<T>& v) {
+        void* h = nullptr;
+        T* d = upload(v, st, h);
+        ptrs.push_back(h);
+        return d;
+    }
+};
+
+inline const double2* pair_ptr(const double2* base, const Ctx& c, int dir, int j) {
+    return base + (long long)dir * c.K * 2 * c.P + (long long)j * 2 * c.P;
+}
+inline double2* pair_ptr(double2* base, const Ctx& c, int dir, int j) {
+    return base + (long long)dir * c.K * 2 * c.P + (long long)j * 2 * c.P;
+}
+
+template <class C>
+void zero_slots(Ctx& ctx, const std::vector<int>& layers, int ldc) {
+    for (int l : layers) {
+        const Shape& sh = ctx.shapes[ctx.layers[l].shape];
+        HZ_CUDA(cudaMemsetAsync(ctx.slot_acc[l], 0, (size_t)sh.N * ldc * sizeof(C), ctx.stream));
+    }
+}
+
+// S_top on layer l (source pair of interface l-1) / S_bot on layer l (pair of interface l)
+template <class C>
+Inject<C> make_inject(Ctx& ctx, int l, bool top, const double2* pair, long long rstride, int ldc, int col0) {
+    const Layer& ly = ctx.layers[l];
+    const Shape& sh = ctx.shapes[ly.shape];
+    Inject<C> q;
+    q.acc = (C*)ctx.slot_acc[l];
+    q.pos = sh.d_pos;
+    q.src = pair;
+    q.rstride = rstride;
+    q.ldc = ldc;
+    q.col0 = col0;
+    const int Pl = (int)ctx.P;
+    if (top) {  // Q_{l-1} = lo gets -c t(P); P_{l-1} = lo-1 gets +c t(Q)
+        q.zl_m = ly.lo - ly.zlo; q.off_m = 0;
+        q.zl_p = ly.lo - 1 - ly.zlo; q.off_p = Pl;
+    } else {    // P_l = hi gets -c t(Q); Q_l = hi+1 gets +c t(P)
+        q.zl_m = ly.hi - ly.zlo; q.off_m = Pl;
+        q.zl_p = ly.hi + 1 - ly.zlo; q.off_p = 0;
+    }
+    return q;
+}
+
+template <class C>
+Extract<C> make_extract(Ctx& ctx, int l, bool bottom, int pl, const std::vector<int>& cols, double2* dst,
+                        long long rstride, int ldc, double sign) {
+    const Layer& ly = ctx.layers[l];
+    const Shape& sh = ctx.shapes[ly.shape];
+    Extract<C> e;
+    e.x = (const C*)ctx.slot_x[l];
+    e.pos = sh.d_pos;
+    e.dst = dst;
+    e.rstride = rstride;
+    e.ldc = ldc;
+    // bottom: planes (P_l, Q_l) = (hi, hi+1); top: (P_{l-1}, Q_{l-1}) = (lo-1, lo)
+    int z = bottom ? (ly.hi + pl) : (ly.lo - 1 + pl);
+    e.zl = z - ly.zlo;
+    e.nblk = (int)cols.size();
+    for (int b = 0; b < 4; ++b) e.cols[b] = b < e.nblk ? cols[b] : 0;
+    e.sign = sign;
+    return e;
+}
+
+template <class C>
+void launch_inject(Ctx& ctx, Scratch& scr, const std::vector<Inject<C>>& v, int R) {
+    if (v.empty()) return;
+    Inject<C>* d = scr.up(v);
+    dim3 grid(cdiv(ctx.P, 256), R, (unsigned)v.size());
+    k_inject<C><<<grid, 256, 0, ctx.stream>>>(d, ctx.d_sx_n, ctx.d_sy_n, 1.0 / (ctx.h * ctx.h), ctx.nx, ctx.ny);
+    HZ_CHECK_LAUNCH();
+}
+
+template <class C>
+void launch_extract(Ctx& ctx, Scratch& scr, const std::vector<Extract<C>>& v, int R) {
+    if (v.empty()) return;
+    Extract<C>* d = scr.up(v);
+    dim3 grid(cdiv(ctx.P, 256), R, (unsigned)v.size());
+    k_extract<C><<<grid, 256, 0, ctx.stream>>>(d, (int)ctx.P);
+    HZ_CHECK_LAUNCH();
+}
+
+void pairs_axpy(Ctx& ctx, double2* y, long long ys, const double2* x, long long xs, double a, const double2* z,
+                long long zs, double b, int zplane, int npairs, int R) {
+    long long n = (long long)npairs * 2 * ctx.P;
+    dim3 grid(cdiv(n, 256), R);
+    k_pairs_axpy<<<grid, 256, 0, ctx.stream>>>(y, ys, x, xs, a, z, zs, b, zplane, npairs, (int)ctx.P);
+    HZ_CHECK_LAUNCH();
+}
+
+std::vector<int> all_layers(const Ctx& ctx) {
+    std::vector<int> v(ctx.L);
+    for (int l = 0; l < ctx.L; ++l) v[l] = l;
+    return v;
+}
+
+template <class C>
+void volume_sources(Ctx& ctx, Scratch& scr, const std::vector<int>& layers, const double2* g, bool scale, int R,
+                    int ldc) {
+    std::vector<VolIO<C>> io;
+    int maxpl = 0;
+    for (int l : layers) {
+        const Layer& ly = ctx.layers[l];
+        VolIO<C> q;
+        q.vec = (C*)ctx.slot_acc[l];
+        q.pos = ctx.shapes[ly.shape].d_pos;
+        q.ldc = ldc; q.col0 = 0; q.lo = ly.lo; q.hi = ly.hi; q.zlo = ly.zlo;
+        io.push_back(q);
+        maxpl = std::max(maxpl, ly.hi - ly.lo + 1);
+    }
+    VolIO<C>* d = scr.up(io);
+    dim3 grid(cdiv(ctx.P, 256), maxpl, (unsigned)io.size());
+    k_volume_source<C><<<grid, 256, 0, ctx.stream>>>(d, g, R, (long long)ctx.nz * ctx.P, ctx.nx, ctx.ny, ctx.d_sx_n,
+                                                     ctx.d_sy_n, ctx.d_sz_n, scale ? 1 : 0);
+    HZ_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// operators
+// ------------------------------------------------------------------------------------------
+template <class C>
+void op_layer_solve(Ctx& ctx, int ell, const double2* g, int ncols, double2* w) {
+    const bool dbl = sizeof(C) == 16;
+    const int ldc = padded_ldc(dbl, ncols);
+    if (ldc > ctx.slot_cap) throw Error{HZ_ERR_ADMISSION, "too many columns for the layer workspace"};
+    const Layer& ly = ctx.layers[ell];
+    const Shape& sh = ctx.shapes[ly.shape];
+    std::vector<int> one{ell};
+    Batch& b = get_batch<C>(ctx, one);
+    zero_slots<C>(ctx, one, ldc);
+    dim3 grid(cdiv(sh.N, 256), ncols);
+    k_gather_local<C><<<grid, 256, 0, ctx.stream>>>((C*)ctx.slot_acc[ell], sh.d_pos, ldc, g, sh.N, ncols);
+    HZ_CHECK_LAUNCH();
+    substitute<C>(b, ncols, ctx.stream);
+    k_scatter_local<C><<<grid, 256, 0, ctx.stream>>>((const C*)ctx.slot_x[ell], sh.d_pos, ldc, w, sh.N, ncols);
+    HZ_CHECK_LAUNCH();
+}
+
+template <class C>
+void op_polarized_rhs(Ctx& ctx, const double2* g, bool scale, int R, double2* fpol) {
+    const bool dbl = sizeof(C) == 16;
+    const int ldc = padded_ldc(dbl, R);
+    if (ldc > ctx.slot_cap) throw Error{HZ_ERR_ADMISSION, "too many columns for the layer workspace"};
+    Scratch scr(ctx.stream);
+    auto layers = all_layers(ctx);
+    Batch& b = get_batch<C>(ctx, layers);
+    zero_slots<C>(ctx, layers, ldc);
+    volume_sources<C>(ctx, scr, layers, g, scale, R, ldc);
+    substitute<C>(b, R, ctx.stream);
+    HZ_CUDA(cudaMemsetAsync(fpol, 0, (size_t)R * ctx.ntr * sizeof(double2), ctx.stream));
+    std::vector<Extract<C>> ex;
+    for (int j = 0; j < ctx.K; ++j)
+        for (int pl = 0; pl < 2; ++pl) {
+            // f_down_j = -(v^j(P_j), v^j(Q_j)); f_up_j = -(v^{j+1}(P_j), v^{j+1}(Q_j))
+            ex.push_back(make_extract<C>(ctx, j, true, pl, {0}, pair_ptr(fpol, ctx, 0, j) + pl * ctx.P, ctx.ntr, ldc, -1.0));
+            ex.push_back(make_extract<C>(ctx, j + 1, false, pl, {0}, pair_ptr(fpol, ctx, 1, j) + pl * ctx.P, ctx.ntr, ldc, -1.0));
+        }
+    launch_extract<C>(ctx, scr, ex, R);
+}
+
+// y = M_pol x: u_down = D_down x_down + U x_up,  u_up = D_up x_up + L x_down.
+template <class C>
+void op_apply_mpol(Ctx& ctx, const double2* x, int R, double2* y) {
+    const bool dbl = sizeof(C) == 16;
+    const int K = ctx.K, L = ctx.L;
+    Scratch scr(ctx.stream);
+    const long long ntr = ctx.ntr;
+    // identity terms: u_down_j = -x_down_j - [P plane] x_up_j ; u_up_j = -x_up_j - [Q plane] x_down_j
+    pairs_axpy(ctx, pair_ptr(y, ctx, 0, 0), ntr, pair_ptr(x, ctx, 0, 0), ntr, -1.0, pair_ptr(x, ctx, 1, 0), ntr,
+               -1.0, 0, K, R);
+    pairs_axpy(ctx, pair_ptr(y, ctx, 1, 0), ntr, pair_ptr(x, ctx, 1, 0), ntr, -1.0, pair_ptr(x, ctx, 0, 0), ntr,
+               -1.0, 1, K, R);
+    // source blocks: 0 = S_top x_down_{l-1}, 1 = S_bot x_down_l, 2 = S_top x_up_{l-1}, 3 = S_bot x_up_l
+    int per_pass = 4;
+    while (per_pass > 1 && padded_ldc(dbl, per_pass * R) > ctx.slot_cap) per_pass /= 2;
+    if (padded_ldc(dbl, R) > ctx.slot_cap) throw Error{HZ_ERR_ADMISSION, "too many columns for the layer workspace"};
+    auto layers = all_layers(ctx);
+    Batch& b = get_batch<C>(ctx, layers);
+    for (int p0 = 0; p0 < 4; p0 += per_pass) {
+        const int nbk = per_pass;
+        const int ncols = nbk * R;
+        const int ldc = padded_ldc(dbl, ncols);
+        zero_slots<C>(ctx, layers, ldc);
+        std::vector<Inject<C>> inj;
+        int colof[4] = {-1, -1, -1, -1};
+        for (int q = 0; q < nbk; ++q) colof[p0 + q] = q * R;
+        for (int l = 0; l < L; ++l)
+            for (int q = 0; q < nbk; ++q) {
+                int blk = p0 + q;
+                bool top = (blk == 0 || blk == 2);
+                int dir = (blk < 2) ? 0 : 1;
+                if (top && l >= 1)
+                    inj.push_back(make_inject<C>(ctx, l, true, pair_ptr(x, ctx, dir, l - 1), ntr, ldc, q * R));
+                if (!top && l <= L - 2)
+                    inj.push_back(make_inject<C>(ctx, l, false, pair_ptr(x, ctx, dir, l), ntr, ldc, q * R));
+            }
+        launch_inject<C>(ctx, scr, inj, R);
+        substitute<C>(b, ncols, ctx.stream);
+        std::vector<Extract<C>> ex;
+        for (int j = 0; j < K; ++j) {
+            // bottom of layer j -> u_down_j: blocks {0 (l>=1), 2 (l>=1), 3}
+            std::vector<int> cb, ct;
+            if (j >= 1 && colof[0] >= 0) cb.push_back(colof[0]);
+            if (j >= 1 && colof[2] >= 0) cb.push_back(colof[2]);
+            if (colof[3] >= 0) cb.push_back(colof[3]);
+            // top of layer j+1 -> u_up_j: blocks {0, 1 (l<=L-2), 3 (l<=L-2)}
+            if (colof[0] >= 0) ct.push_back(colof[0]);
+            if (j + 1 <= L - 2 && colof[1] >= 0) ct.push_back(colof[1]);
+            if (j + 1 <= L - 2 && colof[3] >= 0) ct.push_back(colof[3]);
+            for (int pl = 0; pl < 2; ++pl) {
+                if (!cb.empty())
+                    ex.push_back(make_extract<C>(ctx, j, true, pl, cb, pair_ptr(y, ctx, 0, j) + pl * ctx.P, ntr, ldc, 1.0));
+                if (!ct.empty())
+                    ex.push_back(make_extract<C>(ctx, j + 1, false, pl, ct, pair_ptr(y, ctx, 1, j) + pl * ctx.P, ntr, ldc, 1.0));
+            }
+        }
+        launch_extract<C>(ctx, scr, ex, R);
+    }
+}
+
+// y = P x (Eq. 16): y_down = sweep_down(x_down); s = x_up - L y_down; y_up = sweep_up(s).
+// tmp: one trace vector [R][ntr] of scratch.
+template <class C>
+void op_apply_precond(Ctx& ctx, const double2* x, int R, double2* y, double2* tmp) {
+    const bool dbl = sizeof(C) == 16;
+    const int K = ctx.K, L = ctx.L;
+    const long long ntr = ctx.ntr;
+    const int ldc = padded_ldc(dbl, R);
+    if (ldc > ctx.slot_cap) throw Error{HZ_ERR_ADMISSION, "too many columns for the layer workspace"};
+    Scratch scr(ctx.stream);
+    // downward sweep (Algorithm 4)
+    pairs_axpy(ctx, pair_ptr(y, ctx, 0, 0), ntr, pair_ptr(x, ctx, 0, 0), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
+    for (int j = 1; j < K; ++j) {
+        std::vector<int> one{j};
+        Batch& b = get_batch<C>(ctx, one);
+        zero_slots<C>(ctx, one, ldc);
+        launch_inject<C>(ctx, scr, {make_inject<C>(ctx, j, true, pair_ptr(y, ctx, 0, j - 1), ntr, ldc, 0)}, R);
+        substitute<C>(b, R, ctx.stream);
+        pairs_axpy(ctx, pair_ptr(y, ctx, 0, j), ntr, pair_ptr(x, ctx, 0, j), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
+        std::vector<Extract<C>> ex;
+        for (int pl = 0; pl < 2; ++pl)
+            ex.push_back(make_extract<C>(ctx, j, true, pl, {0}, pair_ptr(y, ctx, 0, j) + pl * ctx.P, ntr, ldc, 1.0));
+        launch_extract<C>(ctx, scr, ex, R);
+    }
+    // upward reflections (Algorithm 6): s_j = x_up_j - ([w]_P, [w]_Q - y_down_j(Q)),
+    // w = G^{j+1} (S_top y_down_j + S_bot y_down_{j+1}); s lives in the up half of tmp
+    double2* s = tmp;
+    pairs_axpy(ctx, pair_ptr(s, ctx, 1, 0), ntr, pair_ptr(x, ctx, 1, 0), ntr, 1.0, pair_ptr(y, ctx, 0, 0), ntr, 1.0,
+               1, K, R);
+    {
+        std::vector<int> layers;
+        for (int l = 1; l < L; ++l) layers.push_back(l);
+        Batch& b = get_batch<C>(ctx, layers);
+        zero_slots<C>(ctx, layers, ldc);
+        std::vector<Inject<C>> inj;
+        for (int l = 1; l < L; ++l) {
+            inj.push_back(make_inject<C>(ctx, l, true, pair_ptr(y, ctx, 0, l - 1), ntr, ldc, 0));
+            if (l <= L - 2) inj.push_back(make_inject<C>(ctx, l, false, pair_ptr(y, ctx, 0, l), ntr, ldc, 0));
+        }
+        launch_inject<C>(ctx, scr, inj, R);
+        substitute<C>(b, R, ctx.stream);
+        std::vector<Extract<C>> ex;
+        for (int j = 0; j < K; ++j)
+            for (int pl = 0; pl < 2; ++pl)
+                ex.push_back(make_extract<C>(ctx, j + 1, false, pl, {0}, pair_ptr(s, ctx, 1, j) + pl * ctx.P, ntr, ldc, -1.0));
+        launch_extract<C>(ctx, scr, ex, R);
+    }
+    // upward sweep (Algorithm 5)
+    pairs_axpy(ctx, pair_ptr(y, ctx, 1, K - 1), ntr, pair_ptr(s, ctx, 1, K - 1), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
+    for (int j = K - 2; j >= 0; --j) {
+        std::vector<int> one{j + 1};
+        Batch& b = get_batch<C>(ctx, one);
+        zero_slots<C>(ctx, one, ldc);
+        launch_inject<C>(ctx, scr, {make_inject<C>(ctx, j + 1, false, pair_ptr(y, ctx, 1, j + 1), ntr, ldc, 0)}, R);
+        substitute<C>(b, R, ctx.stream);
+        pairs_axpy(ctx, pair_ptr(y, ctx, 1, j), ntr, pair_ptr(s, ctx, 1, j), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
+        std::vector<Extract<C>> ex;
+        for (int pl = 0; pl < 2; ++pl)
+            ex.push_back(make_extract<C>(ctx, j + 1, false, pl, {0}, pair_ptr(y, ctx, 1, j) + pl * ctx.P, ntr, ldc, 1.0));
+        launch_extract<C>(ctx, scr, ex, R);
+    }
+}
+
+// u = reconstruction from f and traces t [R][K][2][P] (Algorithm 2, inner solves).
+template <class C>
+void op_reconstruct(Ctx& ctx, const double2* g, bool scale, const double2* t, int R, double2* u, bool accumulate) {
+    const bool dbl = sizeof(C) == 16;
+    const int L = ctx.L;
+    const int ldc = padded_ldc(dbl, R);
+    if (ldc > ctx.slot_cap) throw Error{HZ_ERR_ADMISSION, "too many columns for the layer workspace"};
+    Scratch scr(ctx.stream);
+    auto layers = all_layers(ctx);
+    Batch& b = get_batch<C>(ctx, layers);
+    zero_slots<C>(ctx, layers, ldc);
+    volume_sources<C>(ctx, scr, layers, g, scale, R, ldc);
+    const long long ts = (long long)ctx.K * 2 * ctx.P;
+    std::vector<Inject<C>> inj;
+    for (int l = 0; l < L; ++l) {
+        if (l >= 1) inj.push_back(make_inject<C>(ctx, l, true, t + (long long)(l - 1) * 2 * ctx.P, ts, ldc, 0));
+        if (l <= L - 2) inj.push_back(make_inject<C>(ctx, l, false, t + (long long)l * 2 * ctx.P, ts, ldc, 0));
+    }
+    launch_inject<C>(ctx, scr, inj, R);
+    substitute<C>(b, R, ctx.stream);
+    std::vector<VolIO<C>> io;
+    int maxpl = 0;
+    for (int l : layers) {
+        const Layer& ly = ctx.layers[l];
+        VolIO<C> q;
+        q.vec = (C*)ctx.slot_x[l];
+        q.pos = ctx.shapes[ly.shape].d_pos;
+        q.ldc = ldc; q.col0 = 0; q.lo = ly.lo; q.hi = ly.hi; q.zlo = ly.zlo;
+        io.push_back(q);
+        maxpl = std::max(maxpl, ly.hi - ly.lo + 1);
+    }
+    VolIO<C>* d = scr.up(io);
+    dim3 grid(cdiv(ctx.P, 256), maxpl, (unsigned)io.size());
+    k_volume_out<C><<<grid, 256, 0, ctx.stream>>>(d, u, R, (long long)ctx.nz * ctx.P, (int)ctx.P, accumulate ? 1 : 0);
+    HZ_CHECK_LAUNCH();
+}
+
+void op_volume_residual(Ctx& ctx, const double2* f, bool scale, const double2* u, int R, double2* r, double* norms) {
+    long long N3 = (long long)ctx.nx * ctx.ny * ctx.nz;
+    HZ_CUDA(cudaMemsetAsync(norms, 0, 2 * R * sizeof(double), ctx.stream));
+    dim3 grid(cdiv(N3, 256), R);
+    k_residual<<<grid, 256, 0, ctx.stream>>>(f, u, r, norms, scale ? 1 : 0, ctx.nx, ctx.ny, ctx.nz, ctx.d_sx_n,
+                                             ctx.d_isx_h, ctx.d_sy_n, ctx.d_isy_h, ctx.d_sz_n, ctx.d_isz_h, ctx.d_m,
+                                             ctx.omega * ctx.omega, 1.0 / (ctx.h * ctx.h));
+    HZ_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------------------------------------
+// GMRES on P M_pol u = P f_pol (Eq. 15), x0 = 0, one Krylov space per column, CGS2.
+// Then traces t = u_down + u_up and the volume reconstruction.  Writes u (not accumulated).
+// ------------------------------------------------------------------------------------------
+template <class C>
+void gmres_solve(Ctx& ctx, const double2* g, bool scale, int R, double2* u, const hz_solve_opts& o,
+                 hz_solve_info* info) {
+    cudaStream_t st = ctx.stream;
+    const long long n = ctx.ntr;
+    if (ctx.L == 1 || n == 0) {
+        op_reconstruct<C>(ctx, g, scale, nullptr, R, u, false);
+        if (info) for (int r = 0; r < R; ++r) { info[r].iters = 0; info[r].trace_relres = 0.0; }
+        return;
+    }
+    const int m = std::max(1, std::min(o.restart, o.max_iter));
+    const long long vs = (long long)R * n;  // stride between Krylov vectors
+    std::vector<void*> allocs;
+    auto alloc = [&](size_t bytes) {
+        void* p = nullptr;
+        if (cudaMallocAsync(&p, std::max<size_t>(bytes, 16), st) != cudaSuccess) {
+            cudaGetLastError();
+            for (void* q : allocs) cudaFreeAsync(q, st);
+            allocs.clear();
+            throw Error{HZ_ERR_ADMISSION, "GMRES workspace does not fit in device memory"};
+        }
+        allocs.push_back(p);
+        return p;
+    };
+    double2* V = (double2*)alloc((size_t)(m + 1) * vs * sizeof(double2));
+    double2* w = (double2*)alloc((size_t)vs * sizeof(double2));
+    double2* w2 = (double2*)alloc((size_t)vs * sizeof(double2));
+    double2* tmp = (double2*)alloc((size_t)vs * sizeof(double2));
+    double2* b = (double2*)alloc((size_t)vs * sizeof(double2));
+    double2* xs = (double2*)alloc((size_t)vs * sizeof(double2));
+    GmresState s;
+    s.H = (double2*)alloc((size_t)R * (m + 1) * m * sizeof(double2));
+    s.cs_sn = (double2*)alloc((size_t)R * m * sizeof(double2));
+    s.sn = (double2*)alloc((size_t)R * m * sizeof(double2));
+    s.g = (double2*)alloc((size_t)R * (m + 1) * sizeof(double2));
+    s.dots = (double2*)alloc((size_t)R * (m + 1) * sizeof(double2));
+    s.y = (double2*)alloc((size_t)R * m * sizeof(double2));
+    s.nrm = (double*)alloc(R * sizeof(double));
+    s.invb = (double*)alloc(R * sizeof(double));
+    s.resid = (double*)alloc(R * sizeof(double));
+    double* b0 = (double*)alloc(R * sizeof(double));
+    s.active = (int*)alloc(R * sizeof(int));
+    s.kused = (int*)alloc(R * sizeof(int));
+    const long long half = (long long)ctx.K * 2 * ctx.P;
+    double2* t = (double2*)alloc((size_t)R * half * sizeof(double2));
+    const int TB = 256;
+    const int gblocks = (int)std::min<long long>(1024, std::max<long long>(1, (n + TB - 1) / TB));
+    const dim3 gvec(cdiv(n, TB), R);
+    auto matvec = [&](const double2* in, double2* out) {
+        op_apply_mpol<C>(ctx, in, R, w2);
+        op_apply_precond<C>(ctx, w2, R, out, tmp);
+    };
+    auto norms = [&](const double2* v, double* out) {
+        HZ_CUDA(cudaMemsetAsync(out, 0, R * sizeof(double), st));
+        k_nrm2<<<dim3(gblocks, R), TB, 0, st>>>(v, n, out);
+        HZ_CHECK_LAUNCH();
+    };
+    auto any_active = [&]() {
+        std::vector<int> h(R);
+        HZ_CUDA(cudaMemcpyAsync(h.data(), s.active, R * sizeof(int), cudaMemcpyDeviceToHost, st));
+        HZ_CUDA(cudaStreamSynchronize(st));
+        for (int r = 0; r < R; ++r) if (h[r]) return true;
+        return false;
+    };
+    const double tiny = 1e-300;
+    std::vector<double> h_resid(R), h_b0(R);
+    int total_it = 0;
+    try {
+        // b = P f_pol ; x = 0
+        op_polarized_rhs<C>(ctx, g, scale, R, w);
+        op_apply_precond<C>(ctx, w, R, b, tmp);
+        HZ_CUDA(cudaMemsetAsync(xs, 0, (size_t)vs * sizeof(double2), st));
+        norms(b, b0);
+        {
+            std::vector<int> ones(R, 1);
+            HZ_CUDA(cudaMemcpyAsync(s.active, ones.data(), R * sizeof(int), cudaMemcpyHostToDevice, st));
+            HZ_CUDA(cudaStreamSynchronize(st));
+        }
+        bool first = true;
+        for (;;) {
+            // residual of the preconditioned system: r0 = b - P M x
+            if (first) {
+                HZ_CUDA(cudaMemcpyAsync(w, b, (size_t)vs * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            } else {
+                matvec(xs, w);
+                k_lincomb<<<gvec, TB, 0, st>>>(w, n, 1.0, b, n, -1.0, w, n, n);
+                HZ_CHECK_LAUNCH();
+            }
+            first = false;
+            norms(w, s.nrm);
+            k_gmres_start<<<cdiv(R, 128), 128, 0, st>>>(s, R, m, tiny);
+            HZ_CHECK_LAUNCH();
+            k_scale_vec<<<gvec, TB, 0, st>>>(V, w, n, s.invb);
+            HZ_CHECK_LAUNCH();
+            if (!any_active()) break;
+            for (int j = 0; j < m && total_it < o.max_iter; ++j) {
+                matvec(V + (long long)j * vs, w);
+                HZ_CUDA(cudaMemsetAsync(s.dots, 0, (size_t)R * (m + 1) * sizeof(double2), st));
+                for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+                    HZ_CUDA(cudaMemsetAsync(s.y, 0, (size_t)R * m * sizeof(double2), st));
+                    k_mdot<<<dim3(gblocks, R), TB, 0, st>>>(V, vs, w, n, j + 1, s.y, m);
+                    HZ_CHECK_LAUNCH();
+                    k_maxpy<<<gvec, TB, 0, st>>>(V, vs, w, n, j + 1, s.y, m);
+                    HZ_CHECK_LAUNCH();
+                    k_accum_dots<<<cdiv(R * (j + 1), 128), 128, 0, st>>>(s.dots, s.y, R, m, j + 1);
+                    HZ_CHECK_LAUNCH();
+                }
+                norms(w, s.nrm);
+                k_gmres_arnoldi<<<cdiv(R, 128), 128, 0, st>>>(s, R, m, j, 0.0, b0, o.gmres_tol, tiny);
+                HZ_CHECK_LAUNCH();
+                k_scale_vec<<<gvec, TB, 0, st>>>(V + (long long)(j + 1) * vs, w, n, s.invb);
+                HZ_CHECK_LAUNCH();
+                ++total_it;
+                if (!any_active()) break;
+            }
+            // x += V y for this cycle
+            k_gmres_lsq<<<cdiv(R, 128), 128, 0, st>>>(s, R, m);
+            HZ_CHECK_LAUNCH();
+            k_maxpy_plus<<<gvec, TB, 0, st>>>(V, vs, xs, n, m, s.y, m);
+            HZ_CHECK_LAUNCH();
+            if (!any_active() || total_it >= o.max_iter) break;
+            // columns still active restart from their current iterate
+        }
+        HZ_CUDA(cudaMemcpyAsync(h_resid.data(), s.resid, R * sizeof(double), cudaMemcpyDeviceToHost, st));
+        HZ_CUDA(cudaMemcpyAsync(h_b0.data(), b0, R * sizeof(double), cudaMemcpyDeviceToHost, st));
+        // traces t = x_down + x_up, laid out [R][K][2][P]
+        k_lincomb<<<dim3(cdiv(half, TB), R), TB, 0, st>>>(t, half, 1.0, xs, n, 1.0, xs + half, n, half);
+        HZ_CHECK_LAUNCH();
+        op_reconstruct<C>(ctx, g, scale, t, R, u, false);
+        HZ_CUDA(cudaStreamSynchronize(st));
+    } catch (...) {
+        for (void* p : allocs) cudaFreeAsync(p, st);
+        throw;
+    }
+    for (void* p : allocs) cudaFreeAsync(p, st);
+    HZ_CUDA(cudaStreamSynchronize(st));
+    if (info) {
+        for (int r = 0; r < R; ++r) {
+            info[r].iters = total_it;
+            double nb = sqrt(std::max(h_b0[r], 0.0));
+            info[r].trace_relres = nb > 0 ? h_resid[r] / nb : 0.0;
+        }
+    }
+}
+
+template void op_layer_solve<float2>(Ctx&, int, const double2*, int, double2*);
+template void op_layer_solve<double2>(Ctx&, int, const double2*, int, double2*);
+template void op_polarized_rhs<float2>(Ctx&, const double2*, bool, int, double2*);
+template void op_polarized_rhs<double2>(Ctx&, const double2*, bool, int, double2*);
+template void op_apply_mpol<float2>(Ctx&, const double2*, int, double2*);
+template void op_apply_mpol<double2>(Ctx&, const double2*, int, double2*);
+template void op_apply_precond<float2>(Ctx&, const double2*, int, double2*, double2*);
+template void op_apply_precond<double2>(Ctx&, const double2*, int, double2*, double2*);
+template void op_reconstruct<float2>(Ctx&, const double2*, bool, const double2*, int, double2*, bool);
+template void op_reconstruct<double2>(Ctx&, const double2*, bool, const double2*, int, double2*, bool);
+template void gmres_solve<float2>(Ctx&, const double2*, bool, int, double2*, const hz_solve_opts&, hz_solve_info*);
+template void gmres_solve<double2>(Ctx&, const double2*, bool, int, double2*, const hz_solve_opts&, hz_solve_info*);
+
+}  // namespace hz

@@ -1,0 +1,263 @@
+// Multi-RHS forward/backward substitution through the packed multifrontal factors.
+//
+// This is the local solve w = (H^l)^{-1} g that every step of the online phase calls
+// (Algorithm 2 local and inner solves; Algorithms 4-9 in the sweeps and the blocks of the
+// polarized matrix).  With the diagonal blocks of the fronts stored inverted, each tree
+// node costs four dense products on a block of columns:
+//   forward  (leaves -> root):  z = Linv * acc[own];         acc[upd] -= L21 * z   (scatter)
+//   backward (root -> leaves):  v = Dinv z - L21^T x[upd];   x[own]   = Linv^T * v
+// Nodes of equal height are independent; a launch covers one phase of one height for all
+// layers of a batch.  Every block computes a TILE-row slab of one product for a chunk of
+// CC right-hand-side columns; the factor tile stream is the HBM traffic that bounds the
+// kernel at small column counts.
+#include <algorithm>
+
+#include "hz_internal.cuh"
+#include "hz_ctx.cuh"
+#include "hz_solve.cuh"
+
+namespace hz {
+
+namespace {
+
+enum { FA = 0, FB = 1, BA = 2, BB = 3 };
+
+__device__ inline long long tri_idx(int rt, int ct) { return (long long)rt * (rt + 1) / 2 + ct; }
+
+template <class C> __device__ inline void atomic_sub(C* p, C v);
+template <> __device__ inline void atomic_sub<float2>(float2* p, float2 v) {
+    atomicAdd(&p->x, -v.x);
+    atomicAdd(&p->y, -v.y);
+}
+template <> __device__ inline void atomic_sub<double2>(double2* p, double2 v) {
+    atomicAdd(&p->x, -v.x);
+    atomicAdd(&p->y, -v.y);
+}
+
+template <class C, int CC, int MODE>
+__global__ void __launch_bounds__(256) k_subst(const Task* __restrict__ tasks,
+                                               const JobDev<C>* __restrict__ jobs, int ldc, int nchunks) {
+    constexpr int WC = CC >= 8 ? 8 : CC;  // warps along the columns
+    constexpr int WK = 8 / WC;            // warps along the reduction dimension
+    constexpr int NCT = CC / WC;          // columns per thread
+    constexpr int KPW = TILE / WK;        // reduction indices per warp per tile
+    __shared__ C Ms[TILE][TILE + 1];      // Ms[col][row] of the stored (column-major) tile
+    __shared__ C Xs[TILE][CC];            // Xs[k][c]
+    __shared__ C Red[WK > 1 ? WK : 1][WK > 1 ? TILE * CC : 1];
+
+    const int chunk = blockIdx.x % nchunks;
+    const Task tk = tasks[blockIdx.x / nchunks];
+    const JobDev<C> jb = jobs[tk.job];
+    const NodeDev nd = jb.nodes[tk.node];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int wc = warp % WC, wk = warp / WC;
+    const int col0 = chunk * CC;
+
+    int kt0, kt1;
+    if (MODE == FA) { kt0 = 0; kt1 = tk.tile + 1; }
+    else if (MODE == FB) { kt0 = 0; kt1 = nd.own_t; }
+    else if (MODE == BA) { kt0 = 0; kt1 = nd.upd_t; }
+    else { kt0 = tk.tile; kt1 = nd.own_t; }
+
+    const C* vec = (MODE == FA || MODE == BB) ? jb.acc : jb.x;
+    const int* upd = jb.upd_idx + nd.upd_off;
+
+    C acc[NCT];
+#pragma unroll
+    for (int u = 0; u < NCT; ++u) acc[u] = czero<C>();
+
+    for (int kt = kt0; kt < kt1; ++kt) {
+        const C* mt;
+        if (MODE == FA) mt = jb.fac + (nd.linv_off + tri_idx(tk.tile, kt)) * TILE2;
+        else if (MODE == FB) mt = jb.fac + (nd.l21_off + (long long)tk.tile * nd.own_t + kt) * TILE2;
+        else if (MODE == BA) mt = jb.fac + (nd.l21_off + (long long)kt * nd.own_t + tk.tile) * TILE2;
+        else mt = jb.fac + (nd.linv_off + tri_idx(kt, tk.tile)) * TILE2;
+#pragma unroll
+        for (int i = 0; i < TILE2 / 256; ++i) {
+            int e = t + i * 256;
+            Ms[e / TILE][e % TILE] = mt[e];
+        }
+        for (int e = t; e < TILE * CC; e += 256) {
+            int k = e / CC, c = e % CC;
+            int r = kt * TILE + k;
+            C v = czero<C>();
+            if (MODE == BA) {
+                if (r < nd.nupd) v = vec[(long long)upd[r] * ldc + col0 + c];
+            } else {
+                if (r < nd.nown) v = vec[(long long)(nd.own0 + r) * ldc + col0 + c];
+            }
+            Xs[k][c] = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < KPW; ++kk) {
+            const int k = wk * KPW + kk;
+            const C a = (MODE == FA || MODE == FB) ? Ms[k][lane] : Ms[lane][k];
+#pragma unroll
+            for (int u = 0; u < NCT; ++u) cfma(acc[u], a, Xs[k][wc * NCT + u]);
+        }
+        __syncthreads();
+    }
+
+    if (WK > 1) {
+#pragma unroll
+        for (int u = 0; u < NCT; ++u) Red[wk][lane * CC + wc * NCT + u] = acc[u];
+        __syncthreads();
+        if (wk != 0) return;
+#pragma unroll
+        for (int u = 0; u < NCT; ++u) {
+            C s = czero<C>();
+            for (int q = 0; q < WK; ++q) s = cadd(s, Red[q][lane * CC + wc * NCT + u]);
+            acc[u] = s;
+        }
+    }
+
+    const int row = tk.tile * TILE + lane;
+    if (MODE == FB) {
+        if (row >= nd.nupd) return;
+        C* dst = jb.acc + (long long)upd[row] * ldc + col0 + wc * NCT;
+#pragma unroll
+        for (int u = 0; u < NCT; ++u) atomic_sub(dst + u, acc[u]);
+        return;
+    }
+    if (row >= nd.nown) return;
+    const long long e = (long long)(nd.own0 + row) * ldc + col0 + wc * NCT;
+    if (MODE == FA || MODE == BB) {
+#pragma unroll
+        for (int u = 0; u < NCT; ++u) jb.x[e + u] = acc[u];
+    } else {  // BA: v = Dinv z - L21^T x_upd, kept in the accumulator vector
+        const C di = jb.dinv[nd.own0 + row];
+#pragma unroll
+        for (int u = 0; u < NCT; ++u) jb.acc[e + u] = csub(cmul(di, jb.x[e + u]), acc[u]);
+    }
+}
+
+template <class C, int CC>
+void launch_level(const Batch& b, int h, int mode, int ldc, int ncols, cudaStream_t st) {
+    const int nchunks = ldc / CC;
+    long long off, n;
+    if (mode == FB) { off = b.upd_off[h]; n = b.upd_n[h]; }
+    else { off = b.own_off[h]; n = b.own_n[h]; }
+    if (n == 0) return;
+    const Task* tasks = b.d_tasks + off;
+    const JobDev<C>* jobs = (const JobDev<C>*)b.d_jobs;
+    dim3 grid((unsigned)(n * nchunks));
+    switch (mode) {
+        case FA: k_subst<C, CC, FA><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks); break;
+        case FB: k_subst<C, CC, FB><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks); break;
+        case BA: k_subst<C, CC, BA><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks); break;
+        default: k_subst<C, CC, BB><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks); break;
+    }
+    HZ_CHECK_LAUNCH();
+    (void)ncols;
+}
+
+template <class C, int CC>
+void run_batch(const Batch& b, int ldc, int ncols, cudaStream_t st) {
+    for (int h = 0; h < b.H; ++h) {
+        launch_level<C, CC>(b, h, FA, ldc, ncols, st);
+        launch_level<C, CC>(b, h, FB, ldc, ncols, st);
+    }
+    for (int h = b.H - 1; h >= 0; --h) {
+        launch_level<C, CC>(b, h, BA, ldc, ncols, st);
+        launch_level<C, CC>(b, h, BB, ldc, ncols, st);
+    }
+}
+
+}  // namespace
+
+int chunk_cols(bool is_double, int ncols) {
+    const int cmax = is_double ? 32 : 64;
+    int c = 1;
+    while (c < ncols && c < cmax) c *= 2;
+    return c;
+}
+
+int padded_ldc(bool is_double, int ncols) {
+    const int cc = chunk_cols(is_double, ncols);
+    return (ncols + cc - 1) / cc * cc;
+}
+
+template <class C>
+void substitute(const Batch& b, int ncols, cudaStream_t st) {
+    const bool dbl = sizeof(C) == 16;
+    const int cc = chunk_cols(dbl, ncols);
+    const int ldc = padded_ldc(dbl, ncols);
+    switch (cc) {
+        case 1: run_batch<C, 1>(b, ldc, ncols, st); break;
+        case 2: run_batch<C, 2>(b, ldc, ncols, st); break;
+        case 4: run_batch<C, 4>(b, ldc, ncols, st); break;
+        case 8: run_batch<C, 8>(b, ldc, ncols, st); break;
+        case 16: run_batch<C, 16>(b, ldc, ncols, st); break;
+        case 32: run_batch<C, 32>(b, ldc, ncols, st); break;
+        default:
+            if constexpr (sizeof(C) == 8) run_batch<C, 64>(b, ldc, ncols, st);
+            else throw Error{HZ_ERR_ARG, "chunk width"};
+    }
+}
+
+template <class C>
+Batch& get_batch(Ctx& ctx, const std::vector<int>& layers) {
+    std::string key;
+    for (int l : layers) key += std::to_string(l) + ",";
+    auto it = ctx.batches.find(key);
+    if (it != ctx.batches.end()) return it->second;
+    Batch b;
+    b.layers = layers;
+    int H = 0;
+    for (int l : layers) H = std::max(H, (int)ctx.shapes[ctx.layers[l].shape].levels.size());
+    b.H = H;
+    std::vector<Task> own_all, upd_all;
+    std::vector<std::vector<Task>> own(H), upd(H);
+    for (int j = 0; j < (int)layers.size(); ++j) {
+        const Shape& sh = ctx.shapes[ctx.layers[layers[j]].shape];
+        for (int h = 0; h < (int)sh.levels.size(); ++h)
+            for (int nid : sh.levels[h]) {
+                const Node& nd = sh.nodes[nid];
+                for (int t = 0; t < nd.own_t; ++t) own[h].push_back(Task{j, nid, t, 0});
+                for (int t = 0; t < nd.upd_t; ++t) upd[h].push_back(Task{j, nid, t, 0});
+            }
+    }
+    std::vector<Task> all;
+    for (int h = 0; h < H; ++h) {
+        b.own_off.push_back((long long)all.size());
+        b.own_n.push_back((long long)own[h].size());
+        all.insert(all.end(), own[h].begin(), own[h].end());
+        b.upd_off.push_back((long long)all.size());
+        b.upd_n.push_back((long long)upd[h].size());
+        all.insert(all.end(), upd[h].begin(), upd[h].end());
+    }
+    HZ_CUDA(cudaMalloc(&b.d_tasks, std::max<size_t>(1, all.size()) * sizeof(Task)));
+    HZ_CUDA(cudaMemcpy(b.d_tasks, all.data(), all.size() * sizeof(Task), cudaMemcpyHostToDevice));
+    std::vector<JobDev<C>> jobs;
+    for (int l : layers) {
+        const Layer& ly = ctx.layers[l];
+        const Shape& sh = ctx.shapes[ly.shape];
+        JobDev<C> jd;
+        jd.fac = (const C*)ly.d_fac;
+        jd.dinv = (const C*)ly.d_dinv;
+        jd.nodes = sh.d_nodes;
+        jd.upd_idx = sh.d_upd_idx;
+        jd.acc = (C*)ctx.slot_acc[l];
+        jd.x = (C*)ctx.slot_x[l];
+        jobs.push_back(jd);
+    }
+    HZ_CUDA(cudaMalloc(&b.d_jobs, jobs.size() * sizeof(JobDev<C>)));
+    HZ_CUDA(cudaMemcpy(b.d_jobs, jobs.data(), jobs.size() * sizeof(JobDev<C>), cudaMemcpyHostToDevice));
+    return ctx.batches.emplace(key, b).first->second;
+}
+
+void free_batches(Ctx& ctx) {
+    for (auto& kv : ctx.batches) {
+        cudaFree(kv.second.d_tasks);
+        cudaFree(kv.second.d_jobs);
+    }
+    ctx.batches.clear();
+}
+
+template void substitute<float2>(const Batch&, int, cudaStream_t);
+template void substitute<double2>(const Batch&, int, cudaStream_t);
+template Batch& get_batch<float2>(Ctx&, const std::vector<int>&);
+template Batch& get_batch<double2>(Ctx&, const std::vector<int>&);
+
+}  // namespace hz

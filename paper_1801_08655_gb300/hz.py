@@ -1,0 +1,243 @@
+"""Thin Python binding of the C ABI in ``include/hz.h`` (argument marshalling only).
+
+Every step of the solver runs in the CUDA library ``_lib/libhz.so``; this module only
+loads it, converts arguments and checks status codes.  There is no fallback: if the
+library is missing, importing the binding raises.  PyTorch is used for device memory
+and streams (complex128 tensors are passed by pointer; their interleaved (re, im)
+layout is the ABI's complex layout).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libhz.so")
+
+HZ_OK, HZ_ERR_ARG, HZ_ERR_OOM, HZ_ERR_ADMISSION, HZ_ERR_STATE, HZ_ERR_NONFINITE, HZ_ERR_PIVOT, \
+    HZ_ERR_NO_CONVERGENCE, HZ_ERR_TIMEOUT, HZ_ERR_CUDA = range(10)
+STATUS_NAMES = ["HZ_OK", "HZ_ERR_ARG", "HZ_ERR_OOM", "HZ_ERR_ADMISSION", "HZ_ERR_STATE", "HZ_ERR_NONFINITE",
+                "HZ_ERR_PIVOT", "HZ_ERR_NO_CONVERGENCE", "HZ_ERR_TIMEOUT", "HZ_ERR_CUDA"]
+PREC = {"fp64": 0, "mixed": 1}
+
+EXPORTED = [
+    "hz_default_opts", "hz_create", "hz_factor", "hz_solve", "hz_solve_host", "hz_destroy", "hz_last_error",
+    "hz_layer_info", "hz_factor_stats", "hz_layer_solve_cost", "hz_layer_solve", "hz_polarized_rhs",
+    "hz_apply_mpol", "hz_apply_precond", "hz_reconstruct", "hz_volume_residual",
+]
+
+
+class Grid(ct.Structure):
+    _fields_ = [("nx", ct.c_int32), ("ny", ct.c_int32), ("nz", ct.c_int32), ("h", ct.c_double)]
+
+
+class Pml(ct.Structure):
+    _fields_ = [("npml", ct.c_int32), ("C", ct.c_double), ("npml_local", ct.c_int32)]
+
+
+class SolveOpts(ct.Structure):
+    _fields_ = [("gmres_tol", ct.c_double), ("restart", ct.c_int32), ("max_iter", ct.c_int32),
+                ("refine_tol", ct.c_double), ("max_refine", ct.c_int32)]
+
+
+class SolveInfo(ct.Structure):
+    _fields_ = [("iters", ct.c_int32), ("refinements", ct.c_int32), ("trace_relres", ct.c_double),
+                ("volume_relres", ct.c_double), ("ms_total", ct.c_float)]
+
+
+class HzError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ct.CDLL:
+    """Load libhz.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: build it with paper_1801_08655_gb300.build.build()")
+    lib = ct.CDLL(path)
+    P, I32, D, VP = ct.POINTER, ct.c_int32, ct.c_double, ct.c_void_p
+    lib.hz_default_opts.argtypes = [ct.c_int, P(SolveOpts)]
+    lib.hz_default_opts.restype = None
+    lib.hz_create.argtypes = [P(Grid), VP, D, P(Pml), I32, ct.c_int, VP, P(VP)]
+    lib.hz_factor.argtypes = [VP]
+    lib.hz_solve.argtypes = [VP, VP, I32, VP, P(SolveOpts), P(SolveInfo)]
+    lib.hz_solve_host.argtypes = [VP, VP, I32, VP, P(SolveOpts), P(SolveInfo)]
+    lib.hz_destroy.argtypes = [VP]
+    lib.hz_last_error.argtypes = [VP]
+    lib.hz_last_error.restype = ct.c_char_p
+    lib.hz_layer_info.argtypes = [VP, I32, P(I32), P(I32), P(I32), P(I32)]
+    lib.hz_factor_stats.argtypes = [VP, P(ct.c_int64), P(ct.c_int64), P(D), P(ct.c_int64), P(ct.c_float)]
+    lib.hz_layer_solve_cost.argtypes = [VP, I32, P(D), P(D)]
+    lib.hz_layer_solve.argtypes = [VP, I32, VP, I32, VP]
+    lib.hz_polarized_rhs.argtypes = [VP, VP, I32, VP]
+    lib.hz_apply_mpol.argtypes = [VP, VP, I32, VP]
+    lib.hz_apply_precond.argtypes = [VP, VP, I32, VP]
+    lib.hz_reconstruct.argtypes = [VP, VP, VP, I32, VP]
+    lib.hz_volume_residual.argtypes = [VP, VP, VP, I32, VP, P(D)]
+    for name in EXPORTED:
+        if name not in ("hz_default_opts", "hz_last_error"):
+            getattr(lib, name).restype = ct.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr()) if t is not None else 0
+
+
+def default_opts(precision: str = "mixed") -> SolveOpts:
+    o = SolveOpts()
+    load().hz_default_opts(PREC[precision], ct.byref(o))
+    return o
+
+
+class Solver:
+    """One (grid, m, omega, PML, layers, precision) problem with resident factors."""
+
+    def __init__(self, m: np.ndarray, omega: float, npml: int, C: float, n_layers: int,
+                 precision: str = "mixed", npml_local: int = -1, h: float = 1.0, stream=None):
+        import torch
+        self.lib = load()
+        m = np.ascontiguousarray(np.asarray(m, dtype=np.float64))
+        nz, ny, nx = m.shape
+        self.shape = (nz, ny, nx)
+        self.precision = precision
+        self.n_layers = n_layers
+        self.K = n_layers - 1
+        self.P = nx * ny
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        g = Grid(nx, ny, nz, h)
+        p = Pml(npml, C, npml_local)
+        hnd = ct.c_void_p()
+        st = self.lib.hz_create(ct.byref(g), m.ctypes.data, omega, ct.byref(p), n_layers, PREC[precision],
+                                ct.c_void_p(self.stream.cuda_stream), ct.byref(hnd))
+        if st != HZ_OK:
+            raise HzError(st, self.lib.hz_last_error(None).decode())
+        self.h = hnd
+
+    # -------------------------------------------------------------------- plumbing
+    def _check(self, st: int, allow=(HZ_OK,)):
+        if st not in allow:
+            raise HzError(st, self.lib.hz_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hz_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------------- main path
+    def factor(self):
+        self._check(self.lib.hz_factor(self.h))
+
+    def solve(self, rhs, opts: Optional[SolveOpts] = None, u=None, allow_noconv: bool = False):
+        """rhs: complex128 CUDA tensor (R, nz, ny, nx).  Returns (u, [SolveInfo]*R, status)."""
+        import torch
+        assert rhs.is_cuda and rhs.dtype == torch.complex128 and rhs.is_contiguous()
+        R = rhs.shape[0]
+        if u is None:
+            u = torch.empty_like(rhs)
+        info = (SolveInfo * R)()
+        st = self.lib.hz_solve(self.h, _ptr(rhs), R, _ptr(u), ct.byref(opts) if opts else None, info)
+        self._check(st, (HZ_OK, HZ_ERR_NO_CONVERGENCE) if allow_noconv else (HZ_OK,))
+        return u, list(info), st
+
+    def solve_host(self, rhs: np.ndarray, opts: Optional[SolveOpts] = None, u: Optional[np.ndarray] = None,
+                   allow_noconv: bool = False):
+        """Host (numpy complex128) rhs and u: the end-to-end entry point."""
+        rhs = np.ascontiguousarray(rhs, dtype=np.complex128)
+        R = rhs.shape[0]
+        if u is None:
+            u = np.empty_like(rhs)
+        info = (SolveInfo * R)()
+        st = self.lib.hz_solve_host(self.h, rhs.ctypes.data, R, u.ctypes.data,
+                                    ct.byref(opts) if opts else None, info)
+        self._check(st, (HZ_OK, HZ_ERR_NO_CONVERGENCE) if allow_noconv else (HZ_OK,))
+        return u, list(info), st
+
+    # -------------------------------------------------------------------- introspection
+    def layer_info(self, ell: int):
+        v = [ct.c_int32() for _ in range(4)]
+        self._check(self.lib.hz_layer_info(self.h, ell, *[ct.byref(x) for x in v]))
+        return tuple(x.value for x in v)  # lo, hi, zlo, zhi
+
+    def factor_stats(self):
+        a, b, d = ct.c_int64(), ct.c_int64(), ct.c_int64()
+        f, ms = ct.c_double(), ct.c_float()
+        self._check(self.lib.hz_factor_stats(self.h, ct.byref(a), ct.byref(b), ct.byref(f), ct.byref(d),
+                                             ct.byref(ms)))
+        return dict(nodes=a.value, factor_entries=b.value, factor_flops=f.value, workspace_bytes=d.value,
+                    factor_ms=ms.value)
+
+    def layer_solve_cost(self, ell: int):
+        b, f = ct.c_double(), ct.c_double()
+        self._check(self.lib.hz_layer_solve_cost(self.h, ell, ct.byref(b), ct.byref(f)))
+        return b.value, f.value
+
+    # -------------------------------------------------------------------- stages
+    def layer_solve(self, ell: int, g):
+        """g: complex128 CUDA tensor (ncols, nzl, ny, nx) on layer ell's local grid."""
+        import torch
+        assert g.is_cuda and g.dtype == torch.complex128 and g.is_contiguous()
+        w = torch.empty_like(g)
+        self._check(self.lib.hz_layer_solve(self.h, ell, _ptr(g), g.shape[0], _ptr(w)))
+        return w
+
+    def trace_shape(self, R: int):
+        nz, ny, nx = self.shape
+        return (R, 2, self.K, 2, ny, nx)
+
+    def polarized_rhs(self, rhs):
+        import torch
+        R = rhs.shape[0]
+        out = torch.empty(self.trace_shape(R), dtype=torch.complex128, device=rhs.device)
+        self._check(self.lib.hz_polarized_rhs(self.h, _ptr(rhs), R, _ptr(out)))
+        return out
+
+    def apply_mpol(self, x):
+        import torch
+        y = torch.empty_like(x)
+        self._check(self.lib.hz_apply_mpol(self.h, _ptr(x), x.shape[0], _ptr(y)))
+        return y
+
+    def apply_precond(self, x):
+        import torch
+        y = torch.empty_like(x)
+        self._check(self.lib.hz_apply_precond(self.h, _ptr(x), x.shape[0], _ptr(y)))
+        return y
+
+    def reconstruct(self, rhs, t):
+        import torch
+        u = torch.empty_like(rhs)
+        self._check(self.lib.hz_reconstruct(self.h, _ptr(rhs), _ptr(t), rhs.shape[0], _ptr(u)))
+        return u
+
+    def volume_residual(self, rhs, u, want_r: bool = False):
+        import torch
+        R = rhs.shape[0]
+        r = torch.empty_like(rhs) if want_r else None
+        rel = (ct.c_double * R)()
+        self._check(self.lib.hz_volume_residual(self.h, _ptr(rhs), _ptr(u), R, _ptr(r), rel))
+        return list(rel), r
+
+
+def exported_symbols(path: str = LIB_PATH) -> Sequence[str]:
+    """Names of the declared entry points present in the library (no GPU needed)."""
+    lib = ct.CDLL(path)
+    return [n for n in EXPORTED if hasattr(lib, n)]

@@ -1,0 +1,181 @@
+"""GPU parity of the CUDA path against the CPU oracle, through the C ABI.
+
+Every comparison is element-wise on the same seeded inputs.  Tolerances:
+* FP64 mode: 1e-10 relative (L2) for stages, and the end-to-end solution within 1e-6
+  of the global direct solve (expected ~1e-10).
+* Mixed mode (complex64 factors and local solves): stages within 2e-4 relative (FP32
+  rounding through an unpivoted LDL^T of a PML-padded Helmholtz operator); the end-to-end
+  solution after FP64 defect correction within 1e-5 of the global direct solve.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import direct, discretization as D, polarized
+from paper_1801_08655_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+STAGE_TOL = {"fp64": 1e-10, "mixed": 2e-4}
+E2E_TOL = {"fp64": 1e-6, "mixed": 1e-5}
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def hz():
+    from paper_1801_08655_gb300 import build, hz as _hz
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return _hz
+
+
+def make_solver(hz, p, precision, n_layers=None, npml_local=-1):
+    s = hz.Solver(p.m, p.omega, p.npml, p.C, n_layers or p.n_layers, precision=precision,
+                  npml_local=npml_local)
+    s.factor()
+    return s
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_layer_solve_matches_local_direct_solve(hz, precision):
+    p = W.config(1)
+    s = make_solver(hz, p, precision)
+    parts = D.layer_partition(p.n, p.npml, p.n_layers)
+    rng = np.random.default_rng(5)
+    for ell in range(p.n_layers):
+        lo, hi, zlo, zhi = s.layer_info(ell)
+        assert (zlo, zhi) == D.local_grid(ell, parts, p.n, p.npml)
+        assert (lo, hi) == parts[ell]
+        H = D.local_operator(p.m, p.omega, ell, parts, p.npml, p.npml, p.C).tocsc()
+        nzl = zhi - zlo + 1
+        g = rng.standard_normal((3, nzl, p.n, p.n)) + 1j * rng.standard_normal((3, nzl, p.n, p.n))
+        ref = spla.spsolve(H, g.reshape(3, -1).T).T.reshape(g.shape)
+        w = s.layer_solve(ell, cuda(g)).cpu().numpy()
+        assert rel(w, ref) < STAGE_TOL[precision], (ell, rel(w, ref))
+    s.close()
+
+
+@pytest.fixture(scope="module")
+def small_case():
+    p = W.small_problem(20, 4, 4, seed=31, R=2)
+    M = polarized.PolarizedModel(p.m, p.omega, p.npml, p.C, p.n_layers)
+    return p, M
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_polarized_stages_match_oracle_model(hz, small_case, precision):
+    p, M = small_case
+    s = make_solver(hz, p, precision)
+    f = p.rhs()
+    fpol = s.polarized_rhs(cuda(f)).cpu().numpy()
+    rng = np.random.default_rng(9)
+    shp = s.trace_shape(p.R)
+    x = rng.standard_normal(shp) + 1j * rng.standard_normal(shp)
+    y = s.apply_mpol(cuda(x)).cpu().numpy()
+    z = s.apply_precond(cuda(x)).cpu().numpy()
+    for r in range(p.R):
+        fd, fu = M.polarized_rhs(f[r])
+        assert rel(fpol[r, 0], fd) < STAGE_TOL[precision]
+        assert rel(fpol[r, 1], fu) < STAGE_TOL[precision]
+        yd, yu = M.apply_Mpol(x[r, 0], x[r, 1])
+        assert rel(y[r, 0], yd) < STAGE_TOL[precision]
+        assert rel(y[r, 1], yu) < STAGE_TOL[precision]
+        zd, zu = M.apply_P(x[r, 0], x[r, 1])
+        assert rel(z[r, 0], zd) < STAGE_TOL[precision]
+        assert rel(z[r, 1], zu) < STAGE_TOL[precision]
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_reconstruction_from_exact_traces(hz, small_case, precision):
+    p, M = small_case
+    s = make_solver(hz, p, precision)
+    f = p.rhs()
+    u = direct.solve(p.m, p.omega, p.npml, p.C, f)
+    t = np.stack([M.traces_of(u[r]) for r in range(p.R)])
+    ug = s.reconstruct(cuda(f), cuda(t)).cpu().numpy()
+    assert rel(ug, u) < STAGE_TOL[precision]
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_end_to_end_config1(hz, precision):
+    p = W.config(1)
+    f = p.rhs()
+    u = direct.solve(p.m, p.omega, p.npml, p.C, f)
+    s = make_solver(hz, p, precision)
+    ug, info, st = s.solve(cuda(f))
+    ug = ug.cpu().numpy()
+    err = rel(ug, u)
+    assert err < E2E_TOL[precision], err
+    assert 1 <= info[0].iters <= 10
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("n,npml,L,R", [(20, 4, 4, 3), (24, 4, 6, 5), (16, 3, 1, 2), (18, 3, 2, 1)])
+def test_end_to_end_small(hz, precision, n, npml, L, R):
+    p = W.small_problem(n, npml, L, seed=100 + n + L, R=R)
+    f = p.rhs()
+    u = direct.solve(p.m, p.omega, p.npml, p.C, f)
+    s = make_solver(hz, p, precision)
+    ug, info, st = s.solve(cuda(f))
+    ug = ug.cpu().numpy()
+    for r in range(R):
+        assert rel(ug[r], u[r]) < E2E_TOL[precision], (r, rel(ug[r], u[r]))
+    s.close()
+
+
+def test_batch_equals_alone(hz):
+    """A right-hand side gives the same answer alone and batched with others."""
+    p = W.small_problem(20, 4, 4, seed=77, R=4)
+    f = p.rhs()
+    s = make_solver(hz, p, "mixed")
+    ub, _, _ = s.solve(cuda(f))
+    u1, _, _ = s.solve(cuda(f[2:3]))
+    assert rel(u1.cpu().numpy()[0], ub.cpu().numpy()[2]) < 1e-6
+    s.close()
+
+
+def test_volume_residual_matches_oracle_operator(hz):
+    p = W.small_problem(14, 3, 2, seed=3, R=2)
+    s = make_solver(hz, p, "fp64")
+    rng = np.random.default_rng(1)
+    u = rng.standard_normal((2, 14, 14, 14)) + 1j * rng.standard_normal((2, 14, 14, 14))
+    f = p.rhs()
+    rel_gpu, r = s.volume_residual(cuda(f), cuda(u), want_r=True)
+    A = D.global_operator(p.m, p.omega, p.npml, p.C)
+    S = D.row_scaling(14, p.npml, p.C, p.omega)
+    for q in range(2):
+        ref = (S * f[q]).ravel() - A @ u[q].ravel()
+        assert rel(r[q].cpu().numpy().ravel(), ref) < 1e-13
+        assert rel_gpu[q] == pytest.approx(np.linalg.norm(ref) / np.linalg.norm((S * f[q]).ravel()), rel=1e-10)
+    s.close()
+
+
+def test_errors_are_statuses(hz):
+    p = W.small_problem(12, 3, 2, seed=3, R=1)
+    s = hz.Solver(p.m, p.omega, p.npml, p.C, 2, precision="fp64")
+    with pytest.raises(hz.HzError) as e:
+        s.solve(cuda(p.rhs()))
+    assert e.value.status == hz.HZ_ERR_STATE
+    s.close()
+    with pytest.raises(hz.HzError) as e:
+        hz.Solver(p.m, -1.0, p.npml, p.C, 2)
+    assert e.value.status == hz.HZ_ERR_ARG
+    bad = p.m.copy()
+    bad[3, 3, 3] = np.nan
+    with pytest.raises(hz.HzError) as e:
+        hz.Solver(bad, p.omega, p.npml, p.C, 2)
+    assert e.value.status == hz.HZ_ERR_NONFINITE
