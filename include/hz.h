@@ -190,6 +190,19 @@ hz_status hz_reconstruct(hz_handle* h, const double* rhs, const double* t, int32
 hz_status hz_volume_residual(hz_handle* h, const double* rhs, const double* u, int32_t R,
                              double* r, double* relres_host);
 
+/* ------------------------------------------------------------------------------------
+ * Measurement.  hz_profile_begin starts recording CUDA events around every batched
+ * forward+backward substitution (the kernel family that dominates the online phase);
+ * hz_profile_end synchronizes the handle's stream and returns the number of recorded
+ * substitution calls, their summed device time in ms, and the summed algorithmic factor
+ * bytes (each stored factor entry read once forward and once backward) and real flops.
+ * hz_kernel_launches returns the number of kernels the library has launched in this
+ * process (all handles).
+ * ------------------------------------------------------------------------------------ */
+hz_status hz_profile_begin(hz_handle* h);
+hz_status hz_profile_end(hz_handle* h, int64_t* calls, double* total_ms, double* alg_bytes, double* alg_flops);
+int64_t hz_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

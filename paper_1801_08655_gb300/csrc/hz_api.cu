@@ -14,6 +14,7 @@ using hz::Ctx;
 using hz::Error;
 
 namespace hz {
+std::atomic<long long> g_launch_count{0};
 namespace {
 
 thread_local std::string g_create_error;
@@ -72,6 +73,13 @@ void* dev_alloc(size_t bytes) {
         throw Error{HZ_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed"};
     }
     return d;
+}
+
+// Device-to-host copy ordered after the work queued on the handle's stream (which may be a
+// non-blocking stream that the legacy default stream does not wait for).
+void d2h(Ctx& c, void* dst, const void* src, size_t bytes) {
+    HZ_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c.stream));
+    HZ_CUDA(cudaStreamSynchronize(c.stream));
 }
 
 size_t elem_size(const Ctx& c) { return c.prec == HZ_PREC_FP64 ? sizeof(double2) : sizeof(float2); }
@@ -143,7 +151,7 @@ void do_solve(Ctx& c, const double2* rhs, int R, double2* u, const hz_solve_opts
         if (c.prec == HZ_PREC_FP64) {
             gmres_solve<double2>(c, rhs, true, R, u, o, inf.data());
             op_volume_residual(c, rhs, true, u, R, nullptr, norms);
-            HZ_CUDA(cudaMemcpy(hn.data(), norms, 2 * R * sizeof(double), cudaMemcpyDeviceToHost));
+            d2h(c, hn.data(), norms, 2 * R * sizeof(double));
             for (int r = 0; r < R; ++r) {
                 inf[r].volume_relres = hn[2 * r + 1] > 0 ? std::sqrt(hn[2 * r] / hn[2 * r + 1]) : 0.0;
                 if (!(inf[r].trace_relres <= o.gmres_tol * 1.0001)) st_out = HZ_ERR_NO_CONVERGENCE;
@@ -156,7 +164,7 @@ void do_solve(Ctx& c, const double2* rhs, int R, double2* u, const hz_solve_opts
             try {
                 std::vector<double> g2(R);
                 op_volume_residual(c, rhs, true, u, R, res, norms);
-                HZ_CUDA(cudaMemcpy(hn.data(), norms, 2 * R * sizeof(double), cudaMemcpyDeviceToHost));
+                d2h(c, hn.data(), norms, 2 * R * sizeof(double));
                 for (int r = 0; r < R; ++r) g2[r] = hn[2 * r + 1];
                 auto relres = [&](int r) { return g2[r] > 0 ? std::sqrt(hn[2 * r] / g2[r]) : 0.0; };
                 int passes = 0;
@@ -173,7 +181,7 @@ void do_solve(Ctx& c, const double2* rhs, int R, double2* u, const hz_solve_opts
                     ++passes;
                     for (int r = 0; r < R; ++r) inf[r].iters = inf2[r].iters;
                     op_volume_residual(c, rhs, true, u, R, res, norms);
-                    HZ_CUDA(cudaMemcpy(hn.data(), norms, 2 * R * sizeof(double), cudaMemcpyDeviceToHost));
+                    d2h(c, hn.data(), norms, 2 * R * sizeof(double));
                 }
                 for (int r = 0; r < R; ++r) {
                     inf[r].refinements = passes;
@@ -340,6 +348,7 @@ hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz
             c.layers.push_back(ly);
         }
         c.d_coefs = dev_copy(coefs);
+        HZ_CUDA(cudaDeviceSynchronize());  // uploads complete before any work on the stream
         *out = h;
         return HZ_OK;
     } catch (const Error& e) {
@@ -378,7 +387,7 @@ hz_status hz_factor(hz_handle* h) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         int flag[4];
-        HZ_CUDA(cudaMemcpy(flag, c.d_flag, sizeof(flag), cudaMemcpyDeviceToHost));
+        d2h(c, flag, c.d_flag, sizeof(flag));
         if (flag[0]) throw Error{HZ_ERR_PIVOT, "tiny or non-finite pivot in the unpivoted LDL^T"};
         c.factored = true;
         return HZ_OK;
@@ -583,7 +592,7 @@ hz_status hz_volume_residual(hz_handle* h, const double* rhs, const double* u, i
         std::vector<double> hn(2 * R);
         try {
             op_volume_residual(c, (const double2*)rhs, true, (const double2*)u, R, (double2*)r, norms);
-            HZ_CUDA(cudaMemcpy(hn.data(), norms, 2 * R * sizeof(double), cudaMemcpyDeviceToHost));
+            d2h(c, hn.data(), norms, 2 * R * sizeof(double));
         } catch (...) {
             cudaFree(norms);
             throw;
@@ -594,5 +603,41 @@ hz_status hz_volume_residual(hz_handle* h, const double* rhs, const double* u, i
         return HZ_OK;
     })
 }
+
+hz_status hz_profile_begin(hz_handle* h) {
+    if (!h) return HZ_ERR_ARG;
+    Ctx& c = h->ctx;
+    for (auto& r : c.prof_recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+    c.prof_recs.clear();
+    c.prof = true;
+    return HZ_OK;
+}
+
+hz_status hz_profile_end(hz_handle* h, int64_t* calls, double* total_ms, double* alg_bytes, double* alg_flops) {
+    if (!h) return HZ_ERR_ARG;
+    HZ_TRY(h, {
+        Ctx& c = h->ctx;
+        c.prof = false;
+        HZ_CUDA(cudaStreamSynchronize(c.stream));
+        double ms = 0, by = 0, fl = 0;
+        for (auto& r : c.prof_recs) {
+            float t = 0.f;
+            HZ_CUDA(cudaEventElapsedTime(&t, r.e0, r.e1));
+            ms += t;
+            by += r.bytes;
+            fl += r.flops;
+            cudaEventDestroy(r.e0);
+            cudaEventDestroy(r.e1);
+        }
+        if (calls) *calls = (int64_t)c.prof_recs.size();
+        c.prof_recs.clear();
+        if (total_ms) *total_ms = ms;
+        if (alg_bytes) *alg_bytes = by;
+        if (alg_flops) *alg_flops = fl;
+        return HZ_OK;
+    })
+}
+
+int64_t hz_kernel_launches(void) { return (int64_t)hz::g_launch_count.load(); }
 
 }  // extern "C"

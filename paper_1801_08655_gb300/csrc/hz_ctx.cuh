@@ -29,10 +29,18 @@ struct LayerCoef {
 struct Batch {
     std::vector<int> layers;
     int H = 0;
-    std::vector<long long> own_off, own_n, upd_off, upd_n;  // per level, into d_tasks
+    int KS = 1 << 30;                           // max reduction tiles per task (split-K)
+    std::vector<long long> off[4], cnt[4];      // per phase (FA, FB, BA, BB) and level, into d_tasks
     Task* d_tasks = nullptr;
-    void* d_jobs = nullptr;  // JobDev<C>[njobs]
+    void* d_jobs = nullptr;                     // JobDev<C>[njobs]
+    std::vector<std::pair<void*, void*>> vec_ptrs;  // (acc, x) of each job
+    std::vector<long long> vec_rows;
+    double alg_bytes = 0;       // factor bytes one forward+backward substitution streams (all jobs)
+    double flops_per_col = 0;   // real flops per right-hand-side column (all jobs)
 };
+
+// Event-timed record of substitution calls (enabled by hz_profile_begin).
+struct ProfRec { cudaEvent_t e0, e1; double bytes, flops; };
 
 struct Ctx {
     // problem
@@ -60,6 +68,8 @@ struct Ctx {
     std::vector<void*> slot_acc, slot_x;   // per layer, N_layer * slot_cap complex
     std::map<std::string, Batch> batches;
     std::string last_error;
+    bool prof = false;
+    std::vector<ProfRec> prof_recs;
 };
 
 template <class C> void factor_layers(Ctx& ctx);

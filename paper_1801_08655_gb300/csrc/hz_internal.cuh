@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -158,7 +159,13 @@ struct Error {
         }                                                                                     \
     } while (0)
 
-#define HZ_CHECK_LAUNCH() HZ_CUDA(cudaGetLastError())
+// every kernel launch of the library goes through this check, which also counts it
+extern std::atomic<long long> g_launch_count;
+#define HZ_CHECK_LAUNCH()                                                   \
+    do {                                                                    \
+        ::hz::g_launch_count.fetch_add(1, std::memory_order_relaxed);       \
+        HZ_CUDA(cudaGetLastError());                                        \
+    } while (0)
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 

@@ -572,12 +572,12 @@ void op_layer_solve(Ctx& ctx, int ell, const double2* g, int ncols, double2* w) 
     const Layer& ly = ctx.layers[ell];
     const Shape& sh = ctx.shapes[ly.shape];
     std::vector<int> one{ell};
-    Batch& b = get_batch<C>(ctx, one);
+    Batch& b = get_batch<C>(ctx, one, ncols);
     zero_slots<C>(ctx, one, ldc);
     dim3 grid(cdiv(sh.N, 256), ncols);
     k_gather_local<C><<<grid, 256, 0, ctx.stream>>>((C*)ctx.slot_acc[ell], sh.d_pos, ldc, g, sh.N, ncols);
     HZ_CHECK_LAUNCH();
-    substitute<C>(b, ncols, ctx.stream);
+    substitute<C>(ctx, b, ncols);
     k_scatter_local<C><<<grid, 256, 0, ctx.stream>>>((const C*)ctx.slot_x[ell], sh.d_pos, ldc, w, sh.N, ncols);
     HZ_CHECK_LAUNCH();
 }
@@ -589,10 +589,10 @@ void op_polarized_rhs(Ctx& ctx, const double2* g, bool scale, int R, double2* fp
     if (ldc > ctx.slot_cap) throw Error{HZ_ERR_ADMISSION, "too many columns for the layer workspace"};
     Scratch scr(ctx.stream);
     auto layers = all_layers(ctx);
-    Batch& b = get_batch<C>(ctx, layers);
+    Batch& b = get_batch<C>(ctx, layers, R);
     zero_slots<C>(ctx, layers, ldc);
     volume_sources<C>(ctx, scr, layers, g, scale, R, ldc);
-    substitute<C>(b, R, ctx.stream);
+    substitute<C>(ctx, b, R);
     HZ_CUDA(cudaMemsetAsync(fpol, 0, (size_t)R * ctx.ntr * sizeof(double2), ctx.stream));
     std::vector<Extract<C>> ex;
     for (int j = 0; j < ctx.K; ++j)
@@ -621,11 +621,11 @@ void op_apply_mpol(Ctx& ctx, const double2* x, int R, double2* y) {
     while (per_pass > 1 && padded_ldc(dbl, per_pass * R) > ctx.slot_cap) per_pass /= 2;
     if (padded_ldc(dbl, R) > ctx.slot_cap) throw Error{HZ_ERR_ADMISSION, "too many columns for the layer workspace"};
     auto layers = all_layers(ctx);
-    Batch& b = get_batch<C>(ctx, layers);
     for (int p0 = 0; p0 < 4; p0 += per_pass) {
         const int nbk = per_pass;
         const int ncols = nbk * R;
         const int ldc = padded_ldc(dbl, ncols);
+        Batch& b = get_batch<C>(ctx, layers, ncols);
         zero_slots<C>(ctx, layers, ldc);
         std::vector<Inject<C>> inj;
         int colof[4] = {-1, -1, -1, -1};
@@ -641,7 +641,7 @@ void op_apply_mpol(Ctx& ctx, const double2* x, int R, double2* y) {
                     inj.push_back(make_inject<C>(ctx, l, false, pair_ptr(x, ctx, dir, l), ntr, ldc, q * R));
             }
         launch_inject<C>(ctx, scr, inj, R);
-        substitute<C>(b, ncols, ctx.stream);
+        substitute<C>(ctx, b, ncols);
         std::vector<Extract<C>> ex;
         for (int j = 0; j < K; ++j) {
             // bottom of layer j -> u_down_j: blocks {0 (l>=1), 2 (l>=1), 3}
@@ -678,10 +678,10 @@ void op_apply_precond(Ctx& ctx, const double2* x, int R, double2* y, double2* tm
     pairs_axpy(ctx, pair_ptr(y, ctx, 0, 0), ntr, pair_ptr(x, ctx, 0, 0), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
     for (int j = 1; j < K; ++j) {
         std::vector<int> one{j};
-        Batch& b = get_batch<C>(ctx, one);
+        Batch& b = get_batch<C>(ctx, one, R);
         zero_slots<C>(ctx, one, ldc);
         launch_inject<C>(ctx, scr, {make_inject<C>(ctx, j, true, pair_ptr(y, ctx, 0, j - 1), ntr, ldc, 0)}, R);
-        substitute<C>(b, R, ctx.stream);
+        substitute<C>(ctx, b, R);
         pairs_axpy(ctx, pair_ptr(y, ctx, 0, j), ntr, pair_ptr(x, ctx, 0, j), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
         std::vector<Extract<C>> ex;
         for (int pl = 0; pl < 2; ++pl)
@@ -696,7 +696,7 @@ void op_apply_precond(Ctx& ctx, const double2* x, int R, double2* y, double2* tm
     {
         std::vector<int> layers;
         for (int l = 1; l < L; ++l) layers.push_back(l);
-        Batch& b = get_batch<C>(ctx, layers);
+        Batch& b = get_batch<C>(ctx, layers, R);
         zero_slots<C>(ctx, layers, ldc);
         std::vector<Inject<C>> inj;
         for (int l = 1; l < L; ++l) {
@@ -704,7 +704,7 @@ void op_apply_precond(Ctx& ctx, const double2* x, int R, double2* y, double2* tm
             if (l <= L - 2) inj.push_back(make_inject<C>(ctx, l, false, pair_ptr(y, ctx, 0, l), ntr, ldc, 0));
         }
         launch_inject<C>(ctx, scr, inj, R);
-        substitute<C>(b, R, ctx.stream);
+        substitute<C>(ctx, b, R);
         std::vector<Extract<C>> ex;
         for (int j = 0; j < K; ++j)
             for (int pl = 0; pl < 2; ++pl)
@@ -715,10 +715,10 @@ void op_apply_precond(Ctx& ctx, const double2* x, int R, double2* y, double2* tm
     pairs_axpy(ctx, pair_ptr(y, ctx, 1, K - 1), ntr, pair_ptr(s, ctx, 1, K - 1), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
     for (int j = K - 2; j >= 0; --j) {
         std::vector<int> one{j + 1};
-        Batch& b = get_batch<C>(ctx, one);
+        Batch& b = get_batch<C>(ctx, one, R);
         zero_slots<C>(ctx, one, ldc);
         launch_inject<C>(ctx, scr, {make_inject<C>(ctx, j + 1, false, pair_ptr(y, ctx, 1, j + 1), ntr, ldc, 0)}, R);
-        substitute<C>(b, R, ctx.stream);
+        substitute<C>(ctx, b, R);
         pairs_axpy(ctx, pair_ptr(y, ctx, 1, j), ntr, pair_ptr(s, ctx, 1, j), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
         std::vector<Extract<C>> ex;
         for (int pl = 0; pl < 2; ++pl)
@@ -736,7 +736,7 @@ void op_reconstruct(Ctx& ctx, const double2* g, bool scale, const double2* t, in
     if (ldc > ctx.slot_cap) throw Error{HZ_ERR_ADMISSION, "too many columns for the layer workspace"};
     Scratch scr(ctx.stream);
     auto layers = all_layers(ctx);
-    Batch& b = get_batch<C>(ctx, layers);
+    Batch& b = get_batch<C>(ctx, layers, R);
     zero_slots<C>(ctx, layers, ldc);
     volume_sources<C>(ctx, scr, layers, g, scale, R, ldc);
     const long long ts = (long long)ctx.K * 2 * ctx.P;
@@ -746,7 +746,7 @@ void op_reconstruct(Ctx& ctx, const double2* g, bool scale, const double2* t, in
         if (l <= L - 2) inj.push_back(make_inject<C>(ctx, l, false, t + (long long)l * 2 * ctx.P, ts, ldc, 0));
     }
     launch_inject<C>(ctx, scr, inj, R);
-    substitute<C>(b, R, ctx.stream);
+    substitute<C>(ctx, b, R);
     std::vector<VolIO<C>> io;
     int maxpl = 0;
     for (int l : layers) {

@@ -8,8 +8,10 @@
 //   backward (root -> leaves):  v = Dinv z - L21^T x[upd];   x[own]   = Linv^T * v
 // Nodes of equal height are independent; a launch covers one phase of one height for all
 // layers of a batch.  Every block computes a TILE-row slab of one product for a chunk of
-// CC right-hand-side columns; the factor tile stream is the HBM traffic that bounds the
-// kernel at small column counts.
+// CC right-hand-side columns over a range of at most KS reduction tiles (split-K keeps the
+// top of the tree, where a level has few nodes with long reductions, spread over the whole
+// GPU); partial products are accumulated with vector atomics into zeroed outputs.  The
+// factor tile stream is the HBM traffic that bounds the kernel at small column counts.
 #include <algorithm>
 
 #include "hz_internal.cuh"
@@ -26,17 +28,18 @@ __device__ inline long long tri_idx(int rt, int ct) { return (long long)rt * (rt
 
 template <class C> __device__ inline void atomic_sub(C* p, C v);
 template <> __device__ inline void atomic_sub<float2>(float2* p, float2 v) {
-    atomicAdd(&p->x, -v.x);
-    atomicAdd(&p->y, -v.y);
+    atomicAdd(p, make_float2(-v.x, -v.y));
 }
 template <> __device__ inline void atomic_sub<double2>(double2* p, double2 v) {
     atomicAdd(&p->x, -v.x);
     atomicAdd(&p->y, -v.y);
 }
+template <class C> __device__ inline void atomic_add(C* p, C v) { atomic_sub(p, cneg(v)); }
 
 template <class C, int CC, int MODE>
 __global__ void __launch_bounds__(256) k_subst(const Task* __restrict__ tasks,
-                                               const JobDev<C>* __restrict__ jobs, int ldc, int nchunks) {
+                                               const JobDev<C>* __restrict__ jobs, int ldc, int nchunks,
+                                               int KS) {
     constexpr int WC = CC >= 8 ? 8 : CC;  // warps along the columns
     constexpr int WK = 8 / WC;            // warps along the reduction dimension
     constexpr int NCT = CC / WC;          // columns per thread
@@ -53,11 +56,14 @@ __global__ void __launch_bounds__(256) k_subst(const Task* __restrict__ tasks,
     const int wc = warp % WC, wk = warp / WC;
     const int col0 = chunk * CC;
 
-    int kt0, kt1;
-    if (MODE == FA) { kt0 = 0; kt1 = tk.tile + 1; }
-    else if (MODE == FB) { kt0 = 0; kt1 = nd.own_t; }
-    else if (MODE == BA) { kt0 = 0; kt1 = nd.upd_t; }
-    else { kt0 = tk.tile; kt1 = nd.own_t; }
+    // reduction range of this task: [tk.pad_ (first tile), +KS) within the product's range
+    int kend;
+    if (MODE == FA) kend = tk.tile + 1;
+    else if (MODE == FB) kend = nd.own_t;
+    else if (MODE == BA) kend = nd.upd_t;
+    else kend = nd.own_t;
+    const int kt0 = tk.pad_;
+    const int kt1 = min(kend, kt0 + KS);
 
     const C* vec = (MODE == FA || MODE == BB) ? jb.acc : jb.x;
     const int* upd = jb.upd_idx + nd.upd_off;
@@ -122,45 +128,60 @@ __global__ void __launch_bounds__(256) k_subst(const Task* __restrict__ tasks,
     }
     if (row >= nd.nown) return;
     const long long e = (long long)(nd.own0 + row) * ldc + col0 + wc * NCT;
-    if (MODE == FA || MODE == BB) {
+    if (MODE == FA || MODE == BB) {  // outputs zeroed beforehand (x before the forward, by BA after)
 #pragma unroll
-        for (int u = 0; u < NCT; ++u) jb.x[e + u] = acc[u];
-    } else {  // BA: v = Dinv z - L21^T x_upd, kept in the accumulator vector
-        const C di = jb.dinv[nd.own0 + row];
+        for (int u = 0; u < NCT; ++u) atomic_add(jb.x + e + u, acc[u]);
+    } else {  // BA: v = Dinv z - L21^T x_upd accumulated in acc (zeroed before the backward)
+        if (kt0 == 0) {
+            // the only task that reads z of these rows; it clears them for BB's accumulation
+            const C di = jb.dinv[nd.own0 + row];
 #pragma unroll
-        for (int u = 0; u < NCT; ++u) jb.acc[e + u] = csub(cmul(di, jb.x[e + u]), acc[u]);
+            for (int u = 0; u < NCT; ++u) {
+                acc[u] = csub(acc[u], cmul(di, jb.x[e + u]));
+                jb.x[e + u] = czero<C>();
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < NCT; ++u) atomic_sub(jb.acc + e + u, acc[u]);
     }
 }
 
 template <class C, int CC>
-void launch_level(const Batch& b, int h, int mode, int ldc, int ncols, cudaStream_t st) {
+void launch_level(const Batch& b, int h, int mode, int ldc, cudaStream_t st) {
     const int nchunks = ldc / CC;
-    long long off, n;
-    if (mode == FB) { off = b.upd_off[h]; n = b.upd_n[h]; }
-    else { off = b.own_off[h]; n = b.own_n[h]; }
+    const long long off = b.off[mode][h], n = b.cnt[mode][h];
     if (n == 0) return;
     const Task* tasks = b.d_tasks + off;
     const JobDev<C>* jobs = (const JobDev<C>*)b.d_jobs;
     dim3 grid((unsigned)(n * nchunks));
     switch (mode) {
-        case FA: k_subst<C, CC, FA><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks); break;
-        case FB: k_subst<C, CC, FB><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks); break;
-        case BA: k_subst<C, CC, BA><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks); break;
-        default: k_subst<C, CC, BB><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks); break;
+        case FA: k_subst<C, CC, FA><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks, b.KS); break;
+        case FB: k_subst<C, CC, FB><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks, b.KS); break;
+        case BA: k_subst<C, CC, BA><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks, b.KS); break;
+        default: k_subst<C, CC, BB><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks, b.KS); break;
     }
     HZ_CHECK_LAUNCH();
-    (void)ncols;
+}
+
+template <class C>
+void zero_vectors(const Batch& b, bool x_vec, int ldc, cudaStream_t st) {
+    for (size_t j = 0; j < b.vec_ptrs.size(); ++j) {
+        void* p = x_vec ? b.vec_ptrs[j].second : b.vec_ptrs[j].first;
+        HZ_CUDA(cudaMemsetAsync(p, 0, (size_t)b.vec_rows[j] * ldc * sizeof(C), st));
+    }
 }
 
 template <class C, int CC>
-void run_batch(const Batch& b, int ldc, int ncols, cudaStream_t st) {
+void run_batch(const Batch& b, int ldc, cudaStream_t st) {
+    zero_vectors<C>(b, true, ldc, st);
     for (int h = 0; h < b.H; ++h) {
-        launch_level<C, CC>(b, h, FA, ldc, ncols, st);
-        launch_level<C, CC>(b, h, FB, ldc, ncols, st);
+        launch_level<C, CC>(b, h, FA, ldc, st);
+        launch_level<C, CC>(b, h, FB, ldc, st);
     }
+    zero_vectors<C>(b, false, ldc, st);
     for (int h = b.H - 1; h >= 0; --h) {
-        launch_level<C, CC>(b, h, BA, ldc, ncols, st);
-        launch_level<C, CC>(b, h, BB, ldc, ncols, st);
+        launch_level<C, CC>(b, h, BA, ldc, st);
+        launch_level<C, CC>(b, h, BB, ldc, st);
     }
 }
 
@@ -179,56 +200,84 @@ int padded_ldc(bool is_double, int ncols) {
 }
 
 template <class C>
-void substitute(const Batch& b, int ncols, cudaStream_t st) {
+void substitute(Ctx& ctx, const Batch& b, int ncols) {
     const bool dbl = sizeof(C) == 16;
     const int cc = chunk_cols(dbl, ncols);
     const int ldc = padded_ldc(dbl, ncols);
+    cudaStream_t st = ctx.stream;
+    ProfRec rec{};
+    if (ctx.prof) {
+        HZ_CUDA(cudaEventCreate(&rec.e0));
+        HZ_CUDA(cudaEventCreate(&rec.e1));
+        HZ_CUDA(cudaEventRecord(rec.e0, st));
+    }
     switch (cc) {
-        case 1: run_batch<C, 1>(b, ldc, ncols, st); break;
-        case 2: run_batch<C, 2>(b, ldc, ncols, st); break;
-        case 4: run_batch<C, 4>(b, ldc, ncols, st); break;
-        case 8: run_batch<C, 8>(b, ldc, ncols, st); break;
-        case 16: run_batch<C, 16>(b, ldc, ncols, st); break;
-        case 32: run_batch<C, 32>(b, ldc, ncols, st); break;
+        case 1: run_batch<C, 1>(b, ldc, st); break;
+        case 2: run_batch<C, 2>(b, ldc, st); break;
+        case 4: run_batch<C, 4>(b, ldc, st); break;
+        case 8: run_batch<C, 8>(b, ldc, st); break;
+        case 16: run_batch<C, 16>(b, ldc, st); break;
+        case 32: run_batch<C, 32>(b, ldc, st); break;
         default:
-            if constexpr (sizeof(C) == 8) run_batch<C, 64>(b, ldc, ncols, st);
+            if constexpr (sizeof(C) == 8) run_batch<C, 64>(b, ldc, st);
             else throw Error{HZ_ERR_ARG, "chunk width"};
+    }
+    if (ctx.prof) {
+        HZ_CUDA(cudaEventRecord(rec.e1, st));
+        rec.bytes = b.alg_bytes;
+        rec.flops = b.flops_per_col * ncols;
+        ctx.prof_recs.push_back(rec);
     }
 }
 
 template <class C>
-Batch& get_batch(Ctx& ctx, const std::vector<int>& layers) {
-    std::string key;
+Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols) {
+    // split the reductions when the batch alone cannot fill the GPU (few layers, few chunks)
+    const bool dbl = sizeof(C) == 16;
+    const int nchunks = padded_ldc(dbl, ncols) / chunk_cols(dbl, ncols);
+    const int KS = ((long long)layers.size() * nchunks >= 64) ? (1 << 30) : 8;
+    std::string key = "KS" + std::to_string(KS) + ":";
     for (int l : layers) key += std::to_string(l) + ",";
     auto it = ctx.batches.find(key);
     if (it != ctx.batches.end()) return it->second;
     Batch b;
     b.layers = layers;
+    b.KS = KS;
     int H = 0;
     for (int l : layers) H = std::max(H, (int)ctx.shapes[ctx.layers[l].shape].levels.size());
     b.H = H;
-    std::vector<Task> own_all, upd_all;
-    std::vector<std::vector<Task>> own(H), upd(H);
+    std::vector<std::vector<Task>> lists[4];
+    for (auto& v : lists) v.assign(H, {});
+    auto split = [&](std::vector<Task>& out, int j, int nid, int tile, int k0, int k1) {
+        if (k1 <= k0) { out.push_back(Task{j, nid, tile, k0}); return; }
+        for (int k = k0; k < k1; k += KS) out.push_back(Task{j, nid, tile, k});
+    };
     for (int j = 0; j < (int)layers.size(); ++j) {
         const Shape& sh = ctx.shapes[ctx.layers[layers[j]].shape];
         for (int h = 0; h < (int)sh.levels.size(); ++h)
             for (int nid : sh.levels[h]) {
                 const Node& nd = sh.nodes[nid];
-                for (int t = 0; t < nd.own_t; ++t) own[h].push_back(Task{j, nid, t, 0});
-                for (int t = 0; t < nd.upd_t; ++t) upd[h].push_back(Task{j, nid, t, 0});
+                for (int t = 0; t < nd.own_t; ++t) {
+                    split(lists[0][h], j, nid, t, 0, t + 1);           // FA: Linv row tile t
+                    split(lists[2][h], j, nid, t, 0, nd.upd_t);        // BA: L21^T row tile t (>= 1 task)
+                    split(lists[3][h], j, nid, t, t, nd.own_t);        // BB: Linv^T row tile t
+                }
+                for (int t = 0; t < nd.upd_t; ++t) split(lists[1][h], j, nid, t, 0, nd.own_t);  // FB
             }
     }
     std::vector<Task> all;
-    for (int h = 0; h < H; ++h) {
-        b.own_off.push_back((long long)all.size());
-        b.own_n.push_back((long long)own[h].size());
-        all.insert(all.end(), own[h].begin(), own[h].end());
-        b.upd_off.push_back((long long)all.size());
-        b.upd_n.push_back((long long)upd[h].size());
-        all.insert(all.end(), upd[h].begin(), upd[h].end());
+    for (int mode = 0; mode < 4; ++mode) {
+        b.off[mode].assign(H, 0);
+        b.cnt[mode].assign(H, 0);
+        for (int h = 0; h < H; ++h) {
+            b.off[mode][h] = (long long)all.size();
+            b.cnt[mode][h] = (long long)lists[mode][h].size();
+            all.insert(all.end(), lists[mode][h].begin(), lists[mode][h].end());
+        }
     }
     HZ_CUDA(cudaMalloc(&b.d_tasks, std::max<size_t>(1, all.size()) * sizeof(Task)));
-    HZ_CUDA(cudaMemcpy(b.d_tasks, all.data(), all.size() * sizeof(Task), cudaMemcpyHostToDevice));
+    HZ_CUDA(cudaMemcpyAsync(b.d_tasks, all.data(), all.size() * sizeof(Task), cudaMemcpyHostToDevice, ctx.stream));
+    HZ_CUDA(cudaStreamSynchronize(ctx.stream));
     std::vector<JobDev<C>> jobs;
     for (int l : layers) {
         const Layer& ly = ctx.layers[l];
@@ -241,9 +290,17 @@ Batch& get_batch(Ctx& ctx, const std::vector<int>& layers) {
         jd.acc = (C*)ctx.slot_acc[l];
         jd.x = (C*)ctx.slot_x[l];
         jobs.push_back(jd);
+        b.vec_ptrs.push_back({ctx.slot_acc[l], ctx.slot_x[l]});
+        b.vec_rows.push_back(sh.N);
+        double entries = 0;
+        for (auto& nd : sh.nodes) entries += (double)nd.nown * (nd.nown + 1) / 2.0 + (double)nd.nown * nd.nupd;
+        b.alg_bytes += 2.0 * entries * sizeof(C);
+        b.flops_per_col += sh.solve_flops_per_col;
     }
     HZ_CUDA(cudaMalloc(&b.d_jobs, jobs.size() * sizeof(JobDev<C>)));
-    HZ_CUDA(cudaMemcpy(b.d_jobs, jobs.data(), jobs.size() * sizeof(JobDev<C>), cudaMemcpyHostToDevice));
+    HZ_CUDA(cudaMemcpyAsync(b.d_jobs, jobs.data(), jobs.size() * sizeof(JobDev<C>), cudaMemcpyHostToDevice,
+                            ctx.stream));
+    HZ_CUDA(cudaStreamSynchronize(ctx.stream));
     return ctx.batches.emplace(key, b).first->second;
 }
 
@@ -255,9 +312,9 @@ void free_batches(Ctx& ctx) {
     ctx.batches.clear();
 }
 
-template void substitute<float2>(const Batch&, int, cudaStream_t);
-template void substitute<double2>(const Batch&, int, cudaStream_t);
-template Batch& get_batch<float2>(Ctx&, const std::vector<int>&);
-template Batch& get_batch<double2>(Ctx&, const std::vector<int>&);
+template void substitute<float2>(Ctx&, const Batch&, int);
+template void substitute<double2>(Ctx&, const Batch&, int);
+template Batch& get_batch<float2>(Ctx&, const std::vector<int>&, int);
+template Batch& get_batch<double2>(Ctx&, const std::vector<int>&, int);
 
 }  // namespace hz

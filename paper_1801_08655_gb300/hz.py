@@ -27,6 +27,7 @@ EXPORTED = [
     "hz_default_opts", "hz_create", "hz_factor", "hz_solve", "hz_solve_host", "hz_destroy", "hz_last_error",
     "hz_layer_info", "hz_factor_stats", "hz_layer_solve_cost", "hz_layer_solve", "hz_polarized_rhs",
     "hz_apply_mpol", "hz_apply_precond", "hz_reconstruct", "hz_volume_residual",
+    "hz_profile_begin", "hz_profile_end", "hz_kernel_launches",
 ]
 
 
@@ -84,9 +85,13 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.hz_apply_precond.argtypes = [VP, VP, I32, VP]
     lib.hz_reconstruct.argtypes = [VP, VP, VP, I32, VP]
     lib.hz_volume_residual.argtypes = [VP, VP, VP, I32, VP, P(D)]
+    lib.hz_profile_begin.argtypes = [VP]
+    lib.hz_profile_end.argtypes = [VP, P(ct.c_int64), P(D), P(D), P(D)]
+    lib.hz_kernel_launches.argtypes = []
     for name in EXPORTED:
-        if name not in ("hz_default_opts", "hz_last_error"):
+        if name not in ("hz_default_opts", "hz_last_error", "hz_kernel_launches"):
             getattr(lib, name).restype = ct.c_int
+    lib.hz_kernel_launches.restype = ct.c_int64
     _lib = lib
     return lib
 
@@ -228,6 +233,14 @@ class Solver:
         self._check(self.lib.hz_reconstruct(self.h, _ptr(rhs), _ptr(t), rhs.shape[0], _ptr(u)))
         return u
 
+    def profile_begin(self):
+        self._check(self.lib.hz_profile_begin(self.h))
+
+    def profile_end(self):
+        n, ms, by, fl = ct.c_int64(), ct.c_double(), ct.c_double(), ct.c_double()
+        self._check(self.lib.hz_profile_end(self.h, ct.byref(n), ct.byref(ms), ct.byref(by), ct.byref(fl)))
+        return dict(calls=n.value, ms=ms.value, bytes=by.value, flops=fl.value)
+
     def volume_residual(self, rhs, u, want_r: bool = False):
         import torch
         R = rhs.shape[0]
@@ -235,6 +248,11 @@ class Solver:
         rel = (ct.c_double * R)()
         self._check(self.lib.hz_volume_residual(self.h, _ptr(rhs), _ptr(u), R, _ptr(r), rel))
         return list(rel), r
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process."""
+    return int(load().hz_kernel_launches())
 
 
 def exported_symbols(path: str = LIB_PATH) -> Sequence[str]:

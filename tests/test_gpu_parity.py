@@ -179,3 +179,40 @@ def test_errors_are_statuses(hz):
     with pytest.raises(hz.HzError) as e:
         hz.Solver(bad, p.omega, p.npml, p.C, 2)
     assert e.value.status == hz.HZ_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config2_against_stored_oracle_samples(hz, precision):
+    """64^3 smooth random medium, 8 layers, 16 sources: sampled values of the oracle's
+    global direct solve (tests/golden/make_golden.py) vs the GPU solution."""
+    import os
+    d = np.load(os.path.join(os.path.dirname(__file__), "golden", "cfg2_64cube_smooth_samples.npz"))
+    p = W.config(2)
+    f = p.rhs()
+    s = make_solver(hz, p, precision)
+    u, info, st = s.solve(cuda(f))
+    uu = u.cpu().numpy().reshape(p.R, -1)
+    for r in range(p.R):
+        assert rel(uu[r, d["idx"]], d["u"][r]) < E2E_TOL[precision], (r, rel(uu[r, d["idx"]], d["u"][r]))
+        assert np.linalg.norm(uu[r]) == pytest.approx(d["norms"][r], rel=E2E_TOL[precision])
+    assert max(i.iters for i in info) <= 10
+    s.close()
+
+
+def test_solve_on_a_nonblocking_stream(hz):
+    """Work queued on a non-blocking stream (as torch creates them) is complete before the
+    library reads results back: residual norms and the solution are right."""
+    p = W.small_problem(20, 4, 4, seed=55, R=2)
+    f = p.rhs()
+    u = direct.solve(p.m, p.omega, p.npml, p.C, f)
+    st = torch.cuda.Stream()
+    s = hz.Solver(p.m, p.omega, p.npml, p.C, p.n_layers, precision="mixed", stream=st)
+    s.factor()
+    with torch.cuda.stream(st):
+        fd = cuda(f)
+    st.synchronize()
+    ug, info, _ = s.solve(fd)
+    st.synchronize()
+    assert rel(ug.cpu().numpy(), u) < E2E_TOL["mixed"]
+    assert all(0.0 < i.volume_relres < 1e-8 for i in info)
+    s.close()
