@@ -172,7 +172,7 @@ def run_ours(args):
     hz.load()
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream(device=dev)
-    p = W.config(3)
+    p = W.config(args.config)
     R = args.rhs or p.R
     src = p.sources[:R]
     n = p.n
@@ -306,8 +306,10 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64/f64", "data": "synthetic",
-            "config": {"workload": f"128^3 layered+block medium, PML 10, 16 layers, R={R} point sources, "
-                                   "mixed precision (complex64 local solves, FP64 GMRES + defect correction)",
+            "config": {"workload": (f"128^3 layered+block medium, PML 10, 16 layers, R={R} point sources, "
+                                    "mixed precision (complex64 local solves, FP64 GMRES + defect correction)")
+                       if args.config == 3 else
+                       (f"{n}^3 {W.CONFIG_NAMES[args.config]}, R={R}, mixed precision"),
                        "n": n, "layers": p.n_layers, "R": R, "precision": "mixed",
                        "l2": "inputs larger than L2: ~40 GB of factors streamed every GMRES iteration",
                        "parallelism": f"replicas x{ws}"},
@@ -329,7 +331,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--rhs", type=int, default=0, help="right-hand sides per step (default 128)")
+    ap.add_argument("--rhs", type=int, default=0, help="right-hand sides per step (default: the workload's R)")
+    ap.add_argument("--config", type=int, default=3, choices=[2, 3],
+                    help="3: 128^3 layered+block, R=128 (the headline workload); 2: 64^3 smooth, R=16")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--fp64-rhs", type=int, default=4)
     ap.add_argument("--no-cpu", action="store_true")
