@@ -199,6 +199,26 @@ hz_status hz_volume_residual(hz_handle* h, const double* rhs, const double* u, i
  * hz_kernel_launches returns the number of kernels the library has launched in this
  * process (all handles).
  * ------------------------------------------------------------------------------------ */
+/*
+ * hz_volume_residual_noalloc -- the FP64 volume residual of hz_volume_residual computed
+ * without allocating any memory during the call.  It has no counterpart in the paper: it
+ * exists for callers that cannot allocate device memory where they need the residual (for
+ * example while a stream is being captured into a CUDA graph, inside a host callback, or
+ * when a caching allocator already owns all free device memory).  The per-column sums
+ * the kernel needs live in a fixed device array inside the library instead of a buffer
+ * allocated per call; only buffers the handle already owns and the caller's arrays are used.
+ *   rhs, u     device complex [R][nz][ny][nx] (f, unscaled; and the candidate solution)
+ *   R          1 <= R <= 1024 (the fixed scratch holds 1024 columns); larger R returns
+ *              HZ_ERR_ARG with a message saying so
+ *   r          device complex [R][nz][ny][nx] receiving S f - A u, or NULL
+ *   relres_host  host double[R] receiving ||S f - A u|| / ||S f||
+ * The first call on a device looks up the device address of the fixed array (set-up); make
+ * that first call before any stream capture.  All calls in the process share the array:
+ * calls that overlap on the GPU (different streams or threads at once) race on it.
+ */
+hz_status hz_volume_residual_noalloc(hz_handle* h, const double* rhs, const double* u, int32_t R, double* r,
+                                     double* relres_host);
+
 hz_status hz_profile_begin(hz_handle* h);
 hz_status hz_profile_end(hz_handle* h, int64_t* calls, double* total_ms, double* alg_bytes, double* alg_flops);
 int64_t hz_kernel_launches(void);

@@ -27,7 +27,7 @@ EXPORTED = [
     "hz_default_opts", "hz_create", "hz_factor", "hz_solve", "hz_solve_host", "hz_destroy", "hz_last_error",
     "hz_layer_info", "hz_factor_stats", "hz_layer_solve_cost", "hz_layer_solve", "hz_polarized_rhs",
     "hz_apply_mpol", "hz_apply_precond", "hz_reconstruct", "hz_volume_residual",
-    "hz_profile_begin", "hz_profile_end", "hz_kernel_launches",
+    "hz_profile_begin", "hz_profile_end", "hz_kernel_launches", "hz_volume_residual_noalloc",
 ]
 
 
@@ -85,6 +85,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.hz_apply_precond.argtypes = [VP, VP, I32, VP]
     lib.hz_reconstruct.argtypes = [VP, VP, VP, I32, VP]
     lib.hz_volume_residual.argtypes = [VP, VP, VP, I32, VP, P(D)]
+    lib.hz_volume_residual_noalloc.argtypes = [VP, VP, VP, I32, VP, P(D)]
     lib.hz_profile_begin.argtypes = [VP]
     lib.hz_profile_end.argtypes = [VP, P(ct.c_int64), P(D), P(D), P(D)]
     lib.hz_kernel_launches.argtypes = []
@@ -232,6 +233,14 @@ class Solver:
         u = torch.empty_like(rhs)
         self._check(self.lib.hz_reconstruct(self.h, _ptr(rhs), _ptr(t), rhs.shape[0], _ptr(u)))
         return u
+
+    def volume_residual_noalloc(self, rhs, u, r=None):
+        """As volume_residual, through the entry point that allocates nothing; r (if given)
+        must be a preallocated complex128 CUDA tensor shaped like rhs."""
+        R = rhs.shape[0]
+        rel = (ct.c_double * R)()
+        self._check(self.lib.hz_volume_residual_noalloc(self.h, _ptr(rhs), _ptr(u), R, _ptr(r), rel))
+        return list(rel)
 
     def profile_begin(self):
         self._check(self.lib.hz_profile_begin(self.h))
