@@ -4,6 +4,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <cstdlib>
 #include <new>
 
 #include "hz_internal.cuh"
@@ -173,9 +174,13 @@ void do_solve(Ctx& c, const double2* rhs, int R, double2* u, const hz_solve_opts
                     for (int r = 0; r < R; ++r) worst = std::max(worst, relres(r));
                     if (!std::isfinite(worst)) { st_out = HZ_ERR_NONFINITE; break; }
                     if (worst <= o.refine_tol || passes >= o.max_refine) break;
-                    // defect correction: A du = r with the mixed path, u += du
+                    // defect correction: A du = r with the mixed path, u += du.  The correction
+                    // only needs the digits that bring the residual below refine_tol, so its GMRES
+                    // tolerance is relaxed accordingly (never looser than 1e-3).
                     std::vector<hz_solve_info> inf2(R);
-                    gmres_solve<float2>(c, res, false, R, du, o, inf2.data());
+                    hz_solve_opts o2 = o;
+                    o2.gmres_tol = std::max(o.gmres_tol, std::min(1e-3, 0.1 * o.refine_tol / std::max(worst, 1e-300)));
+                    gmres_solve<float2>(c, res, false, R, du, o2, inf2.data());
                     k_axpy_vol<<<cdiv((long long)R * N3, 256), 256, 0, c.stream>>>(u, du, (long long)R * N3);
                     HZ_CHECK_LAUNCH();
                     ++passes;
@@ -201,6 +206,12 @@ void do_solve(Ctx& c, const double2* rhs, int R, double2* u, const hz_solve_opts
         throw;
     }
     cudaFree(norms);
+    int flags[4];
+    d2h(c, flags, c.d_flag, sizeof(flags));
+    if (flags[1]) {
+        HZ_CUDA(cudaMemset(c.d_flag + 1, 0, sizeof(int)));
+        throw Error{HZ_ERR_TIMEOUT, "a tensor-core substitution block gave up waiting on its MMAs"};
+    }
     HZ_CUDA(cudaEventRecord(e1, c.stream));
     HZ_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -348,6 +359,9 @@ hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz
             c.layers.push_back(ly);
         }
         c.d_coefs = dev_copy(coefs);
+        if (const char* e = std::getenv("HZ_SUBST_TC")) c.use_tc = std::atoi(e) != 0;
+        if (const char* e = std::getenv("HZ_TC_KS")) c.tc_ks = std::max(1, std::atoi(e));
+        if (const char* e = std::getenv("HZ_TC_MIN_TILES")) c.tc_min_tiles = std::max(1, std::atoi(e));
         HZ_CUDA(cudaDeviceSynchronize());  // uploads complete before any work on the stream
         *out = h;
         return HZ_OK;

@@ -31,6 +31,8 @@ struct Batch {
     int H = 0;
     int KS = 1 << 30;                           // max reduction tiles per task (split-K)
     std::vector<long long> off[4], cnt[4];      // per phase (FA, FB, BA, BB) and level, into d_tasks
+    int KS_tc = 1 << 30;                        // split-K of the tensor-core tasks (tiles)
+    std::vector<long long> pair_off[4], pair_cnt[4];  // tensor-core tasks: two output tiles each
     Task* d_tasks = nullptr;
     void* d_jobs = nullptr;                     // JobDev<C>[njobs]
     std::vector<std::pair<void*, void*>> vec_ptrs;  // (acc, x) of each job
@@ -69,6 +71,9 @@ struct Ctx {
     std::map<std::string, Batch> batches;
     std::string last_error;
     bool prof = false;
+    bool use_tc = false;    // tensor-core substitution for complex64 at >= 64 columns (opt-in)
+    int tc_ks = 4;          // split-K (factor tiles per block) of small tensor-core batches
+    int tc_min_tiles = 3;   // output tiles a node product needs to run on the tensor cores
     std::vector<ProfRec> prof_recs;
 };
 

@@ -7,6 +7,8 @@
 namespace hz {
 
 int chunk_cols(bool is_double, int ncols);
+int tc_columns(int ldc);   // tensor-core column tile for this leading dimension (0: not usable)
+void launch_level_tc(const Batch& b, int h, int mode, int ldc, int* flag, cudaStream_t st);
 int padded_ldc(bool is_double, int ncols);
 
 // Job set with per-level task lists, cached by layer list.

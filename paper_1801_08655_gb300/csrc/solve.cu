@@ -72,29 +72,49 @@ __global__ void __launch_bounds__(256) k_subst(const Task* __restrict__ tasks,
 #pragma unroll
     for (int u = 0; u < NCT; ++u) acc[u] = czero<C>();
 
+    // register-staged prefetch: the next tile's loads are in flight while this tile is used
+    constexpr int XPT = (TILE * CC + 255) / 256;   // vector elements per thread per tile
+    auto mat_ptr = [&](int kt) -> const C* {
+        if (MODE == FA) return jb.fac + (nd.linv_off + tri_idx(tk.tile, kt)) * TILE2;
+        if (MODE == FB) return jb.fac + (nd.l21_off + (long long)tk.tile * nd.own_t + kt) * TILE2;
+        if (MODE == BA) return jb.fac + (nd.l21_off + (long long)kt * nd.own_t + tk.tile) * TILE2;
+        return jb.fac + (nd.linv_off + tri_idx(kt, tk.tile)) * TILE2;
+    };
+    C pm[TILE2 / 256], px[XPT];
+    auto fetch = [&](int kt) {
+        const C* mt = mat_ptr(kt);
+#pragma unroll
+        for (int i = 0; i < TILE2 / 256; ++i) pm[i] = mt[t + i * 256];
+#pragma unroll
+        for (int i = 0; i < XPT; ++i) {
+            const int e = t + i * 256;
+            C v = czero<C>();
+            if (e < TILE * CC) {
+                const int k = e / CC, c = e % CC;
+                const int r = kt * TILE + k;
+                if (MODE == BA) {
+                    if (r < nd.nupd) v = vec[(long long)upd[r] * ldc + col0 + c];
+                } else {
+                    if (r < nd.nown) v = vec[(long long)(nd.own0 + r) * ldc + col0 + c];
+                }
+            }
+            px[i] = v;
+        }
+    };
+    if (kt0 < kt1) fetch(kt0);
     for (int kt = kt0; kt < kt1; ++kt) {
-        const C* mt;
-        if (MODE == FA) mt = jb.fac + (nd.linv_off + tri_idx(tk.tile, kt)) * TILE2;
-        else if (MODE == FB) mt = jb.fac + (nd.l21_off + (long long)tk.tile * nd.own_t + kt) * TILE2;
-        else if (MODE == BA) mt = jb.fac + (nd.l21_off + (long long)kt * nd.own_t + tk.tile) * TILE2;
-        else mt = jb.fac + (nd.linv_off + tri_idx(kt, tk.tile)) * TILE2;
 #pragma unroll
         for (int i = 0; i < TILE2 / 256; ++i) {
-            int e = t + i * 256;
-            Ms[e / TILE][e % TILE] = mt[e];
+            const int e = t + i * 256;
+            Ms[e / TILE][e % TILE] = pm[i];
         }
-        for (int e = t; e < TILE * CC; e += 256) {
-            int k = e / CC, c = e % CC;
-            int r = kt * TILE + k;
-            C v = czero<C>();
-            if (MODE == BA) {
-                if (r < nd.nupd) v = vec[(long long)upd[r] * ldc + col0 + c];
-            } else {
-                if (r < nd.nown) v = vec[(long long)(nd.own0 + r) * ldc + col0 + c];
-            }
-            Xs[k][c] = v;
+#pragma unroll
+        for (int i = 0; i < XPT; ++i) {
+            const int e = t + i * 256;
+            if (e < TILE * CC) Xs[e / CC][e % CC] = px[i];
         }
         __syncthreads();
+        if (kt + 1 < kt1) fetch(kt + 1);
 #pragma unroll 4
         for (int kk = 0; kk < KPW; ++kk) {
             const int k = wk * KPW + kk;
@@ -172,16 +192,20 @@ void zero_vectors(const Batch& b, bool x_vec, int ldc, cudaStream_t st) {
 }
 
 template <class C, int CC>
-void run_batch(const Batch& b, int ldc, cudaStream_t st) {
+void run_batch(const Batch& b, int ldc, bool tc, int* flag, cudaStream_t st) {
     zero_vectors<C>(b, true, ldc, st);
     for (int h = 0; h < b.H; ++h) {
-        launch_level<C, CC>(b, h, FA, ldc, st);
-        launch_level<C, CC>(b, h, FB, ldc, st);
+        for (int mode : {FA, FB}) {
+            launch_level<C, CC>(b, h, mode, ldc, st);
+            if (tc) launch_level_tc(b, h, mode, ldc, flag, st);
+        }
     }
     zero_vectors<C>(b, false, ldc, st);
     for (int h = b.H - 1; h >= 0; --h) {
-        launch_level<C, CC>(b, h, BA, ldc, st);
-        launch_level<C, CC>(b, h, BB, ldc, st);
+        for (int mode : {BA, BB}) {
+            launch_level<C, CC>(b, h, mode, ldc, st);
+            if (tc) launch_level_tc(b, h, mode, ldc, flag, st);
+        }
     }
 }
 
@@ -211,15 +235,17 @@ void substitute(Ctx& ctx, const Batch& b, int ncols) {
         HZ_CUDA(cudaEventCreate(&rec.e1));
         HZ_CUDA(cudaEventRecord(rec.e0, st));
     }
+    const bool tc = (sizeof(C) == 8) && ctx.use_tc && tc_columns(ldc) > 0;
+    int* flag = ctx.d_flag + 1;
     switch (cc) {
-        case 1: run_batch<C, 1>(b, ldc, st); break;
-        case 2: run_batch<C, 2>(b, ldc, st); break;
-        case 4: run_batch<C, 4>(b, ldc, st); break;
-        case 8: run_batch<C, 8>(b, ldc, st); break;
-        case 16: run_batch<C, 16>(b, ldc, st); break;
-        case 32: run_batch<C, 32>(b, ldc, st); break;
+        case 1: run_batch<C, 1>(b, ldc, false, flag, st); break;
+        case 2: run_batch<C, 2>(b, ldc, false, flag, st); break;
+        case 4: run_batch<C, 4>(b, ldc, false, flag, st); break;
+        case 8: run_batch<C, 8>(b, ldc, false, flag, st); break;
+        case 16: run_batch<C, 16>(b, ldc, false, flag, st); break;
+        case 32: run_batch<C, 32>(b, ldc, false, flag, st); break;
         default:
-            if constexpr (sizeof(C) == 8) run_batch<C, 64>(b, ldc, st);
+            if constexpr (sizeof(C) == 8) run_batch<C, 64>(b, ldc, tc, flag, st);
             else throw Error{HZ_ERR_ARG, "chunk width"};
     }
     if (ctx.prof) {
@@ -230,42 +256,76 @@ void substitute(Ctx& ctx, const Batch& b, int ncols) {
     }
 }
 
+// Tensor-core eligibility of one node product: enough output and reduction tiles to fill a
+// 128-row block for more than one stage.
+static bool tc_node(int mode, const Node& nd, int min_tiles) {
+    const int out_t = mode == 1 ? nd.upd_t : nd.own_t;
+    const int red_t = mode == 2 ? nd.upd_t : nd.own_t;
+    return out_t >= min_tiles && red_t >= 2;
+}
+
 template <class C>
 Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols) {
     // split the reductions when the batch alone cannot fill the GPU (few layers, few chunks)
     const bool dbl = sizeof(C) == 16;
-    const int nchunks = padded_ldc(dbl, ncols) / chunk_cols(dbl, ncols);
+    const int ldc = padded_ldc(dbl, ncols);
+    const int nchunks = ldc / chunk_cols(dbl, ncols);
+    const bool tc = !dbl && ctx.use_tc && tc_columns(ldc) > 0;
     const int KS = ((long long)layers.size() * nchunks >= 64) ? (1 << 30) : 8;
-    std::string key = "KS" + std::to_string(KS) + ":";
+    std::string key = "KS" + std::to_string(KS) + "n" + std::to_string(ldc) + (tc ? "tc" : "") + ":";
     for (int l : layers) key += std::to_string(l) + ",";
     auto it = ctx.batches.find(key);
     if (it != ctx.batches.end()) return it->second;
     Batch b;
     b.layers = layers;
     b.KS = KS;
+    const int nchunks_tc = tc ? ldc / tc_columns(ldc) : 1;
+    b.KS_tc = ((long long)layers.size() * nchunks_tc >= 32) ? (1 << 30) : ctx.tc_ks;
     int H = 0;
     for (int l : layers) H = std::max(H, (int)ctx.shapes[ctx.layers[l].shape].levels.size());
     b.H = H;
-    std::vector<std::vector<Task>> lists[4];
+    std::vector<std::vector<Task>> lists[4], quads[4];
     for (auto& v : lists) v.assign(H, {});
-    auto split = [&](std::vector<Task>& out, int j, int nid, int tile, int k0, int k1) {
+    for (auto& v : quads) v.assign(H, {});
+    auto split = [&](std::vector<Task>& out, int j, int nid, int tile, int k0, int k1, int ks) {
         if (k1 <= k0) { out.push_back(Task{j, nid, tile, k0}); return; }
-        for (int k = k0; k < k1; k += KS) out.push_back(Task{j, nid, tile, k});
+        for (int k = k0; k < k1; k += ks) out.push_back(Task{j, nid, tile, k});
     };
     for (int j = 0; j < (int)layers.size(); ++j) {
         const Shape& sh = ctx.shapes[ctx.layers[layers[j]].shape];
         for (int h = 0; h < (int)sh.levels.size(); ++h)
             for (int nid : sh.levels[h]) {
                 const Node& nd = sh.nodes[nid];
-                for (int t = 0; t < nd.own_t; ++t) {
-                    split(lists[0][h], j, nid, t, 0, t + 1);           // FA: Linv row tile t
-                    split(lists[2][h], j, nid, t, 0, nd.upd_t);        // BA: L21^T row tile t (>= 1 task)
-                    split(lists[3][h], j, nid, t, t, nd.own_t);        // BB: Linv^T row tile t
+                for (int mode = 0; mode < 4; ++mode) {
+                    const int out_t = mode == 1 ? nd.upd_t : nd.own_t;
+                    if (tc && tc_node(mode, nd, ctx.tc_min_tiles)) {
+                        for (int t = 0; t < out_t; t += 4) {
+                            if (mode == 0) split(quads[0][h], j, nid, t, 0, std::min(t + 4, nd.own_t), b.KS_tc);
+                            if (mode == 1) split(quads[1][h], j, nid, t, 0, nd.own_t, b.KS_tc);
+                            if (mode == 2) split(quads[2][h], j, nid, t, 0, nd.upd_t, b.KS_tc);
+                            if (mode == 3) split(quads[3][h], j, nid, t, t, nd.own_t, b.KS_tc);
+                        }
+                    } else {
+                        for (int t = 0; t < out_t; ++t) {
+                            if (mode == 0) split(lists[0][h], j, nid, t, 0, t + 1, KS);      // FA: Linv row tile t
+                            if (mode == 1) split(lists[1][h], j, nid, t, 0, nd.own_t, KS);   // FB: L21 row tile t
+                            if (mode == 2) split(lists[2][h], j, nid, t, 0, nd.upd_t, KS);   // BA (>= 1 task)
+                            if (mode == 3) split(lists[3][h], j, nid, t, t, nd.own_t, KS);   // BB
+                        }
+                    }
                 }
-                for (int t = 0; t < nd.upd_t; ++t) split(lists[1][h], j, nid, t, 0, nd.own_t);  // FB
             }
     }
     std::vector<Task> all;
+    for (int mode = 0; mode < 4; ++mode) {
+        b.pair_off[mode].assign(H, 0);
+        b.pair_cnt[mode].assign(H, 0);
+        for (int h = 0; h < H; ++h) {
+            b.pair_off[mode][h] = (long long)all.size();
+            b.pair_cnt[mode][h] = (long long)quads[mode][h].size();
+            all.insert(all.end(), quads[mode][h].begin(), quads[mode][h].end());
+        }
+    }
     for (int mode = 0; mode < 4; ++mode) {
         b.off[mode].assign(H, 0);
         b.cnt[mode].assign(H, 0);

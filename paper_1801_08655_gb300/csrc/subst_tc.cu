@@ -1,0 +1,385 @@
+// Tensor-core (tcgen05) variant of the substitution products for complex64 factors.
+//
+// A block computes 128 complex output rows (four factor tile rows) x NT right-hand-side
+// columns of one of the four node products of the substitution (see solve.cu), for the
+// nodes whose products are large enough to fill it; smaller nodes of the same tree level run
+// on the CUDA-core kernel in the same phase.
+//
+// The complex product Y = A X is four real products with two accumulators in tensor memory:
+//     Yr = Ar Xr - Ai Xi,    Yi = Ai Xr + Ar Xi,
+// (the minus sign through the instruction descriptor's negate-A bit).  Each real product runs
+// in TF32 with a three-term split of both operands (a = a_hi + a_lo, x = x_hi + x_lo;
+// a x ~ a_hi x_hi + a_hi x_lo + a_lo x_hi) and FP32 accumulation, which keeps every product at
+// FP32-level accuracy (about 2^-21 relative): 12 MMAs (M = 128, N = NT, K = 8) per 8 complex
+// reduction indices.
+//
+// Pipeline (256 threads, 16 complex reduction indices per stage):
+//   raw stage  : cp.async 16-byte copies of the factor tiles and vector rows into shared memory,
+//                two stages ahead; masked rows / absent tiles are zero-filled by the copy;
+//   conversion : shared -> shared, split into hi/lo TF32 operands in the K-major core-matrix
+//                layout (no swizzle), 16-byte conflict-free stores;
+//   MMA        : one thread issues the 24 MMAs of a stage and commits them to an mbarrier that
+//                releases the converted buffer two stages later.
+// The epilogue reads both accumulators from tensor memory (tcgen05.ld; lane = complex row) and
+// accumulates into the solve vectors exactly like the CUDA-core kernel.  Every mbarrier wait is
+// bounded and block-uniform; on timeout the block records an error flag, waits once more
+// (bounded) for its own MMAs, frees its tensor memory and exits.
+#include <algorithm>
+
+#include "hz_internal.cuh"
+#include "hz_ctx.cuh"
+#include "hz_solve.cuh"
+
+namespace hz {
+
+namespace {
+
+enum { FA = 0, FB = 1, BA = 2, BB = 3 };
+
+constexpr int KC = 16;                 // complex reduction indices per stage
+constexpr int LBO = 128;               // bytes between core matrices along K
+constexpr int SBO = (KC / 4) * 128;    // bytes between 8-row groups (K = 16 tf32 per row)
+constexpr int MR = 128;                // complex output rows per block (4 tiles)
+constexpr int TROW = KC * 8 + 16;      // padded raw row (transposed tiles): 144 bytes
+constexpr long long WAIT_LIMIT = 1LL << 26;
+
+__device__ inline long long tri_idx(int rt, int ct) { return (long long)rt * (rt + 1) / 2 + ct; }
+
+__device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline uint64_t smem_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(LBO >> 4) << 16;
+    d |= (uint64_t)(SBO >> 4) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version; base offset 0; no swizzle
+    return d;
+}
+
+// byte offset of (row, k) in a [rows x KC] K-major core-matrix operand (4-byte elements)
+__device__ inline int coff(int row, int k) { return (row >> 3) * SBO + (k >> 2) * LBO + (row & 7) * 16 + (k & 3) * 4; }
+
+__device__ inline float tf32_hi(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
+// 16-byte asynchronous global->shared copy; src_bytes = 0 zero-fills without reading
+__device__ inline void cp16(uint32_t dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long long it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ inline void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                 :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+template <int NT> struct Layout {
+    static constexpr int A_MAT = MR * KC * 4;            // one real operand matrix (8 KB)
+    static constexpr int X_MAT = NT * KC * 4;
+    static constexpr int CONV = 4 * A_MAT + 4 * X_MAT;   // Ar_h Ar_l Ai_h Ai_l  Xr_h Xr_l Xi_h Xi_l
+    static constexpr int RAW_A = 4 * 32 * TROW;          // large enough for both raw tile layouts
+    static constexpr int RAW_X = KC * NT * 8;
+    static constexpr int RAW = RAW_A + RAW_X;
+    static constexpr int TOTAL = 2 * CONV + 2 * RAW + 64;
+};
+
+template <int NT, int MODE>
+__global__ void __launch_bounds__(256, 1) k_subst_tc(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ jobs,
+                                                     int ldc, int nchunks, int KS, int* flag) {
+    using LY = Layout<NT>;
+    constexpr bool TR = (MODE == BA || MODE == BB);  // factor tiles used transposed
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* conv = smem;
+    unsigned char* raw = smem + 2 * LY::CONV;
+    uint64_t* bars = (uint64_t*)(raw + 2 * LY::RAW);
+    uint32_t* tptr = (uint32_t*)(bars + 2);
+
+    const int chunk = blockIdx.x % nchunks;
+    const Task tk = tasks[blockIdx.x / nchunks];
+    const JobDev<float2> jb = jobs[tk.job];
+    const NodeDev nd = jb.nodes[tk.node];
+    const int t = threadIdx.x, w = t >> 5, l = t & 31;
+    const int col0 = chunk * NT;
+    const int o0 = tk.tile;  // first of the four output tiles
+    const int nout_t = (MODE == FB) ? nd.upd_t : nd.own_t;
+    const int kbeg = tk.pad_;
+    int kend = (MODE == FA) ? min(o0 + 4, nd.own_t) : ((MODE == BA) ? nd.upd_t : nd.own_t);
+    kend = min(kend, kbeg + KS);
+    const int nst = max(0, kend - kbeg) * 2;
+    const float2* vec = (MODE == FA || MODE == BB) ? jb.acc : jb.x;
+    const int* upd = jb.upd_idx + nd.upd_off;
+    const int nrows_k = (MODE == BA) ? nd.nupd : nd.nown;   // valid vector rows
+
+    // issue the raw copies of stage s into raw buffer s % 2 (all threads)
+    auto load_raw = [&](int s) {
+        if (s >= nst) return;
+        unsigned char* rb = raw + (s & 1) * LY::RAW;
+        const int kt = kbeg + (s >> 1), hk = s & 1;
+        // factor tiles: 4 output tiles x 16 reduction indices = 1024 chunks of 16 bytes
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int c = t + 256 * i;
+            const int oi = c >> 8, q = c & 255;
+            const int o = o0 + oi;
+            bool exists = o < nout_t;
+            if (MODE == FA) exists = exists && kt <= o;
+            if (MODE == BB) exists = exists && kt >= o;
+            long long toff = 0;
+            if (exists) {
+                if (MODE == FA) toff = nd.linv_off + tri_idx(o, kt);
+                else if (MODE == FB) toff = nd.l21_off + (long long)o * nd.own_t + kt;
+                else if (MODE == BA) toff = nd.l21_off + (long long)kt * nd.own_t + o;
+                else toff = nd.linv_off + tri_idx(kt, o);
+            }
+            const float2* tl = jb.fac + toff * TILE2;
+            uint32_t dst;
+            const float2* src;
+            if (!TR) {  // stored (r, k) at r + 32 k: columns 16 hk .. +16 are contiguous; raw [oi][k][r]
+                dst = smem_u32(rb + oi * 4096 + q * 16);
+                src = tl + hk * KC * 32 + q * 2;
+            } else {    // stored (k, r) at k + 32 r: row r's 16 entries are contiguous; raw [oi][r][k], 144 B rows
+                const int r = q >> 3, j = q & 7;
+                dst = smem_u32(rb + oi * 32 * TROW + r * TROW + j * 16);
+                src = tl + 32 * r + hk * KC + j * 2;
+            }
+            cp16(dst, exists ? (const void*)src : (const void*)jb.fac, exists ? 16 : 0);
+        }
+        // vector rows: KC rows x NT columns, raw [k][n]
+        for (int c = t; c < KC * NT / 2; c += 256) {
+            const int k = c / (NT / 2), j = c % (NT / 2);
+            const int rr = kt * TILE + hk * KC + k;
+            const bool v = rr < nrows_k;
+            long long row = 0;
+            if (v) row = (MODE == BA) ? (long long)upd[rr] : (long long)(nd.own0 + rr);
+            const float2* src = vec + row * ldc + col0 + 2 * j;
+            cp16(smem_u32(rb + LY::RAW_A + k * NT * 8 + j * 16), src, v ? 16 : 0);
+        }
+    };
+
+    if (w == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(tptr)), "r"(2 * NT));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (t == 0)
+        for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bars + b)), "r"(1));
+    load_raw(0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    load_raw(1);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tptr;
+    const uint32_t tm_r = tmem, tm_i = tmem + NT;  // accumulators: real part cols [0, NT), imag [NT, 2NT)
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(MR >> 4) << 24);
+    const uint32_t idesc_neg = idesc | (1u << 13);
+
+    bool ok = true;
+    for (int s = 0; s < nst; ++s) {
+        const int cb = s & 1;
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncthreads();  // raw stage s complete for every thread
+        if (s >= 2) {     // converted buffer cb is free once the MMAs of stage s-2 are done
+            const bool got = mbar_wait(smem_u32(bars + cb), (uint32_t)(((s >> 1) - 1) & 1));
+            ok = __syncthreads_and(got) != 0;
+            if (!ok) break;
+        }
+        unsigned char* rb = raw + cb * LY::RAW;
+        unsigned char* cv = conv + cb * LY::CONV;
+        // ---- convert factor operand: 128 rows x 16 k, thread -> (row, 4 consecutive k)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int id = t + 256 * i;
+            const int row = id & 127, kq = id >> 7;
+            const int oi = row >> 5, r = row & 31;
+            float re[4], im[4];
+            if (!TR) {
+                const float2* src = (const float2*)(rb + oi * 4096);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) { float2 a = src[(4 * kq + j) * 32 + r]; re[j] = a.x; im[j] = a.y; }
+            } else {
+                const float4* src = (const float4*)(rb + oi * 32 * TROW + r * TROW + kq * 32);
+                float4 a0 = src[0], a1 = src[1];
+                re[0] = a0.x; im[0] = a0.y; re[1] = a0.z; im[1] = a0.w;
+                re[2] = a1.x; im[2] = a1.y; re[3] = a1.z; im[3] = a1.w;
+            }
+            float4 rh, rl, ih, il;
+            rh.x = tf32_hi(re[0]); rh.y = tf32_hi(re[1]); rh.z = tf32_hi(re[2]); rh.w = tf32_hi(re[3]);
+            ih.x = tf32_hi(im[0]); ih.y = tf32_hi(im[1]); ih.z = tf32_hi(im[2]); ih.w = tf32_hi(im[3]);
+            rl = make_float4(re[0] - rh.x, re[1] - rh.y, re[2] - rh.z, re[3] - rh.w);
+            il = make_float4(im[0] - ih.x, im[1] - ih.y, im[2] - ih.z, im[3] - ih.w);
+            const int off = coff(row, 4 * kq);
+            *(float4*)(cv + 0 * LY::A_MAT + off) = rh;
+            *(float4*)(cv + 1 * LY::A_MAT + off) = rl;
+            *(float4*)(cv + 2 * LY::A_MAT + off) = ih;
+            *(float4*)(cv + 3 * LY::A_MAT + off) = il;
+        }
+        // ---- convert vector operand: NT rows (columns n) x 16 k
+        for (int id = t; id < NT * 4; id += 256) {
+            const int n = id % NT, kq = id / NT;
+            const float2* src = (const float2*)(rb + LY::RAW_A);
+            float re[4], im[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { float2 a = src[(4 * kq + j) * NT + n]; re[j] = a.x; im[j] = a.y; }
+            float4 rh, rl, ih, il;
+            rh.x = tf32_hi(re[0]); rh.y = tf32_hi(re[1]); rh.z = tf32_hi(re[2]); rh.w = tf32_hi(re[3]);
+            ih.x = tf32_hi(im[0]); ih.y = tf32_hi(im[1]); ih.z = tf32_hi(im[2]); ih.w = tf32_hi(im[3]);
+            rl = make_float4(re[0] - rh.x, re[1] - rh.y, re[2] - rh.z, re[3] - rh.w);
+            il = make_float4(im[0] - ih.x, im[1] - ih.y, im[2] - ih.z, im[3] - ih.w);
+            const int off = 4 * LY::A_MAT + coff(n, 4 * kq);
+            *(float4*)(cv + off + 0 * LY::X_MAT) = rh;
+            *(float4*)(cv + off + 1 * LY::X_MAT) = rl;
+            *(float4*)(cv + off + 2 * LY::X_MAT) = ih;
+            *(float4*)(cv + off + 3 * LY::X_MAT) = il;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // conversion visible to the tensor core; raw buffer cb free
+        load_raw(s + 2);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t base = smem_u32(cv);
+#pragma unroll
+            for (int ks = 0; ks < KC / 8; ++ks) {
+                const uint32_t ko = ks * 2 * LBO;
+                const uint64_t arh = smem_desc(base + 0 * LY::A_MAT + ko), arl = smem_desc(base + 1 * LY::A_MAT + ko);
+                const uint64_t aih = smem_desc(base + 2 * LY::A_MAT + ko), ail = smem_desc(base + 3 * LY::A_MAT + ko);
+                const uint32_t xb = base + 4 * LY::A_MAT + ko;
+                const uint64_t xrh = smem_desc(xb), xrl = smem_desc(xb + LY::X_MAT);
+                const uint64_t xih = smem_desc(xb + 2 * LY::X_MAT), xil = smem_desc(xb + 3 * LY::X_MAT);
+                const uint32_t first = (s == 0 && ks == 0) ? 0u : 1u;
+                // Yr = Ar Xr - Ai Xi
+                mma_tf32(tm_r, arh, xrh, idesc, first);
+                mma_tf32(tm_r, arh, xrl, idesc, 1u);
+                mma_tf32(tm_r, arl, xrh, idesc, 1u);
+                mma_tf32(tm_r, aih, xih, idesc_neg, 1u);
+                mma_tf32(tm_r, aih, xil, idesc_neg, 1u);
+                mma_tf32(tm_r, ail, xih, idesc_neg, 1u);
+                // Yi = Ai Xr + Ar Xi
+                mma_tf32(tm_i, aih, xrh, idesc, first);
+                mma_tf32(tm_i, aih, xrl, idesc, 1u);
+                mma_tf32(tm_i, ail, xrh, idesc, 1u);
+                mma_tf32(tm_i, arh, xih, idesc, 1u);
+                mma_tf32(tm_i, arh, xil, idesc, 1u);
+                mma_tf32(tm_i, arl, xih, idesc, 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(bars + cb)));
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (ok && nst > 0) {
+        const bool got = mbar_wait(smem_u32(bars + ((nst - 1) & 1)), (uint32_t)(((nst - 1) >> 1) & 1));
+        ok = __syncthreads_and(got) != 0;
+    }
+    if (!ok) {
+        if (t == 0) atomicExch(flag, 1);
+        if (nst > 0) mbar_wait(smem_u32(bars + ((nst - 1) & 1)), (uint32_t)(((nst - 1) >> 1) & 1));
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    // ---- epilogue: warp w reads lanes 32 (w % 4) .. +31 (= output tile o0 + w % 4), column half w / 4
+    if (ok) {
+        const int q4 = w & 3;
+        const int row = (o0 + q4) * TILE + l;
+        const bool valid = (o0 + q4) < nout_t && row < ((MODE == FB) ? nd.nupd : nd.nown);
+        const int cbeg = (w >> 2) * (NT / 2);
+        for (int c0 = cbeg; c0 < cbeg + NT / 2; c0 += 16) {
+            uint32_t vr[16], vi[16];
+            if (nst > 0) {
+                const uint32_t lane_off = (uint32_t)(32 * q4) << 16;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]), "=r"(vr[7]),
+                               "=r"(vr[8]), "=r"(vr[9]), "=r"(vr[10]), "=r"(vr[11]), "=r"(vr[12]), "=r"(vr[13]), "=r"(vr[14]), "=r"(vr[15])
+                             : "r"(tm_r + lane_off + (uint32_t)c0));
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]), "=r"(vi[7]),
+                               "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]), "=r"(vi[13]), "=r"(vi[14]), "=r"(vi[15])
+                             : "r"(tm_i + lane_off + (uint32_t)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) { vr[j] = 0u; vi[j] = 0u; }
+            }
+            if (!valid) continue;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                float2 y = make_float2(__uint_as_float(vr[j]), __uint_as_float(vi[j]));
+                const int col = col0 + c0 + j;
+                if (MODE == FB) {
+                    atomicAdd(jb.acc + (long long)upd[row] * ldc + col, make_float2(-y.x, -y.y));
+                } else {
+                    const long long eidx = (long long)(nd.own0 + row) * ldc + col;
+                    if (MODE == FA || MODE == BB) {
+                        atomicAdd(jb.x + eidx, y);
+                    } else {  // BA: acc += Dinv z - partial; the first split clears z
+                        if (kbeg == 0) {
+                            const float2 di = jb.dinv[nd.own0 + row];
+                            const float2 z = jb.x[eidx];
+                            y = csub(y, cmul(di, z));
+                            jb.x[eidx] = make_float2(0.f, 0.f);
+                        }
+                        atomicAdd(jb.acc + eidx, make_float2(-y.x, -y.y));
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(2 * NT));
+}
+
+template <int NT, int MODE>
+void launch_one(const Task* tasks, long long n, const JobDev<float2>* jobs, int ldc, int KS, int* flag, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        HZ_CUDA(cudaFuncSetAttribute(k_subst_tc<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, Layout<NT>::TOTAL));
+        attr = true;
+    }
+    const int nchunks = ldc / NT;
+    k_subst_tc<NT, MODE><<<(unsigned)(n * nchunks), 256, Layout<NT>::TOTAL, st>>>(tasks, jobs, ldc, nchunks, KS, flag);
+    HZ_CHECK_LAUNCH();
+}
+
+template <int NT>
+void launch_mode(const Batch& b, int h, int mode, int ldc, int* flag, cudaStream_t st) {
+    const long long off = b.pair_off[mode][h], n = b.pair_cnt[mode][h];
+    if (n == 0) return;
+    const Task* tasks = b.d_tasks + off;
+    const JobDev<float2>* jobs = (const JobDev<float2>*)b.d_jobs;
+    switch (mode) {
+        case FA: launch_one<NT, FA>(tasks, n, jobs, ldc, b.KS_tc, flag, st); break;
+        case FB: launch_one<NT, FB>(tasks, n, jobs, ldc, b.KS_tc, flag, st); break;
+        case BA: launch_one<NT, BA>(tasks, n, jobs, ldc, b.KS_tc, flag, st); break;
+        default: launch_one<NT, BB>(tasks, n, jobs, ldc, b.KS_tc, flag, st); break;
+    }
+}
+
+}  // namespace
+
+int tc_columns(int ldc) {
+    if (ldc % 128 == 0) return 128;
+    if (ldc % 64 == 0) return 64;
+    return 0;
+}
+
+void launch_level_tc(const Batch& b, int h, int mode, int ldc, int* flag, cudaStream_t st) {
+    if (tc_columns(ldc) == 128) launch_mode<128>(b, h, mode, ldc, flag, st);
+    else launch_mode<64>(b, h, mode, ldc, flag, st);
+}
+
+}  // namespace hz

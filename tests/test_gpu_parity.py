@@ -216,3 +216,54 @@ def test_solve_on_a_nonblocking_stream(hz):
     assert rel(ug.cpu().numpy(), u) < E2E_TOL["mixed"]
     assert all(0.0 < i.volume_relres < 1e-8 for i in info)
     s.close()
+
+
+@pytest.mark.parametrize("ncols", [64, 128, 130])
+def test_tensor_core_layer_solve(hz, ncols, monkeypatch):
+    """With the tensor-core path enabled, mixed-precision layer solves with >= 64 columns run on
+    the tcgen05 kernel (split TF32); they must match the local direct solve within the stage
+    tolerance."""
+    monkeypatch.setenv("HZ_SUBST_TC", "1")
+    p = W.config(1)
+    s = make_solver(hz, p, "mixed")
+    parts = D.layer_partition(p.n, p.npml, p.n_layers)
+    rng = np.random.default_rng(ncols)
+    ell = 1
+    lo, hi, zlo, zhi = s.layer_info(ell)
+    H = D.local_operator(p.m, p.omega, ell, parts, p.npml, p.npml, p.C).tocsc()
+    g = rng.standard_normal((ncols, zhi - zlo + 1, p.n, p.n)) + 1j * rng.standard_normal((ncols, zhi - zlo + 1, p.n, p.n))
+    ref = spla.spsolve(H, g.reshape(ncols, -1).T).T.reshape(g.shape)
+    w = s.layer_solve(ell, cuda(g)).cpu().numpy()
+    for c in (0, ncols // 2, ncols - 1):
+        assert rel(w[c], ref[c]) < STAGE_TOL["mixed"], (c, rel(w[c], ref[c]))
+    s.close()
+
+
+def test_tensor_core_polarized_stages(hz, small_case, monkeypatch):
+    """M_pol on 4R = 128 stacked columns takes the tensor-core path when it is enabled."""
+    monkeypatch.setenv("HZ_SUBST_TC", "1")
+    p, M = small_case
+    s = make_solver(hz, p, "mixed")
+    rng = np.random.default_rng(21)
+    R = 32
+    shp = s.trace_shape(R)
+    x = rng.standard_normal(shp) + 1j * rng.standard_normal(shp)
+    y = s.apply_mpol(cuda(x)).cpu().numpy()
+    for r in (0, 17, 31):
+        yd, yu = M.apply_Mpol(x[r, 0], x[r, 1])
+        assert rel(y[r, 0], yd) < STAGE_TOL["mixed"]
+        assert rel(y[r, 1], yu) < STAGE_TOL["mixed"]
+    s.close()
+
+
+def test_tensor_core_and_cuda_core_paths_agree(hz, monkeypatch):
+    p = W.config(2)
+    f = p.rhs()
+    outs = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("HZ_SUBST_TC", flag)
+        s = make_solver(hz, p, "mixed")
+        u, info, _ = s.solve(cuda(f))
+        outs.append(u.cpu().numpy())
+        s.close()
+    assert rel(outs[0], outs[1]) < 1e-8
