@@ -215,6 +215,7 @@ def run_ours(args):
         step_infos.append(infos)
     stream.synchronize()
     prof = s.profile_end()
+    tuning = [ln for ln in s.tuning_report().splitlines() if ln]
     launches = hz.kernel_launches() - launches0
     torch.cuda.synchronize()
     if ws > 1:
@@ -324,11 +325,70 @@ def run_ours(args):
                            "max_refine": opts.max_refine, "restart": opts.restart},
             "factor_s": factor_s, "factor_tflops": fstats["factor_flops"] / factor_s / 1e12,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "autotune": tuning,
             "clocks": clk, "fp64_gpu": fp64,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_batched(args):
+    """Batched uneven workload: 6 independent problems (40^3..96^3, 4..12 layers, R = 1..64,
+    differing omega) solved together by hz_solve_group, each on its own stream with its matrix-
+    vector product replayed as a CUDA graph; compared with solving them one after another."""
+    import torch
+    from paper_1801_08655_gb300 import build, hz, workloads as W
+    torch.cuda.set_device(0)
+    build.build()
+    probs = W.config(4)
+    solvers, rhs = [], []
+    t0 = time.perf_counter()
+    for p in probs:
+        st = torch.cuda.Stream()
+        s = hz.Solver(p.m, p.omega, p.npml, p.C, p.n_layers, precision="mixed", stream=st)
+        s.factor()
+        solvers.append(s)
+        with torch.cuda.stream(st):
+            f = torch.from_numpy(p.rhs()).cuda()
+        rhs.append(f)
+    torch.cuda.synchronize()
+    factor_s = time.perf_counter() - t0
+    opts = hz.default_opts("mixed")
+    opts.gmres_tol = args.gmres_tol
+    opts.refine_tol = args.refine_tol
+    Rtot = sum(p.R for p in probs)
+    for _ in range(args.warmup):
+        hz.solve_group(solvers, rhs, opts)
+    torch.cuda.synchronize()
+    launches0 = hz.kernel_launches()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        us, infos, sts = hz.solve_group(solvers, rhs, opts)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    launches = hz.kernel_launches() - launches0
+    # the same problems one after another (no overlap)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for s, f in zip(solvers, rhs):
+            s.solve(f, opts)
+    torch.cuda.synchronize()
+    dts = (time.perf_counter() - t0) / args.steps
+    line = {
+        "metric": "online solves/s, batched uneven problems (hz_solve_group)", "value": Rtot / dt, "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64/f64", "data": "synthetic",
+        "config": {"workload": "6 problems " + ", ".join(f"{p.n}^3 L={p.n_layers} R={p.R}" for p in probs),
+                   "precision": "mixed"},
+        "sequential_value": Rtot / dts, "batching_speedup": dts / dt, "factor_s": factor_s,
+        "gpu_launches": launches,
+        "volume_relres_max": max(max(i.volume_relres for i in inf) for inf in infos),
+        "iters": [inf[0].iters for inf in infos],
+    }
+    print(json.dumps(line), flush=True)
+    for s in solvers:
+        s.close()
 
 
 def main():
@@ -338,8 +398,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--rhs", type=int, default=0, help="right-hand sides per step (default: the workload's R)")
-    ap.add_argument("--config", type=int, default=3, choices=[2, 3],
-                    help="3: 128^3 layered+block, R=128 (the headline workload); 2: 64^3 smooth, R=16")
+    ap.add_argument("--config", type=int, default=3, choices=[2, 3, 4],
+                    help="3: 128^3 layered+block, R=128 (the headline workload); 2: 64^3 smooth, R=16; "
+                         "4: six uneven problems solved as one batch")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--fp64-rhs", type=int, default=4)
     ap.add_argument("--no-cpu", action="store_true")
@@ -348,6 +409,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == 4:
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -67,7 +67,7 @@ typedef struct { int32_t npml; double C; int32_t npml_local; } hz_pml;
 
 typedef struct {
     double gmres_tol;    /* stop when ||P(f - M u)|| <= tol ||P f|| per column (default 1e-10 FP64, 1e-7 mixed) */
-    int32_t restart;     /* Krylov dimension before restart (default 20) */
+    int32_t restart;     /* Krylov dimension before restart (default 12) */
     int32_t max_iter;    /* total GMRES iterations cap (default 100) */
     double refine_tol;   /* mixed mode: stop refining when ||S f - A u|| <= refine_tol ||S f|| (default 1e-9) */
     int32_t max_refine;  /* mixed mode: maximum defect-correction passes (default 3) */
@@ -122,6 +122,24 @@ hz_status hz_factor(hz_handle* h);
  */
 hz_status hz_solve(hz_handle* h, const double* rhs, int32_t R, double* u,
                    const hz_solve_opts* opts, hz_solve_info* info);
+
+/*
+ * hz_solve_group -- batched online phase for n independent problems of different sizes and
+ * right-hand-side counts (one handle each, all factored).  Every member is solved as by
+ * hz_solve on its own handle's stream, all members at once (one host thread per member), so
+ * the device overlaps their launches; each member's GMRES matrix-vector product is replayed
+ * as a CUDA graph.  Give every handle its own stream, otherwise the members serialise.
+ *   hs        n distinct handles (a handle may appear once)
+ *   rhs, u    per member: device complex [R[i]][nz][ny][nx] of that member's grid
+ *   R         per member right-hand-side counts
+ *   opts      NULL for each member's defaults
+ *   info      NULL, or n pointers to arrays of R[i] entries (each may be NULL)
+ *   statuses  NULL or n statuses
+ * Returns HZ_OK or the first member's failure status.
+ */
+hz_status hz_solve_group(hz_handle* const* hs, int32_t n, const double* const* rhs, const int32_t* R,
+                         double* const* u, const hz_solve_opts* opts, hz_solve_info* const* info,
+                         hz_status* statuses);
 
 /*
  * hz_solve_host -- as hz_solve with HOST rhs and u: copies rhs to the device, solves,
@@ -222,6 +240,13 @@ hz_status hz_volume_residual_noalloc(hz_handle* h, const double* rhs, const doub
 hz_status hz_profile_begin(hz_handle* h);
 hz_status hz_profile_end(hz_handle* h, int64_t* calls, double* total_ms, double* alg_bytes, double* alg_flops);
 int64_t hz_kernel_launches(void);
+
+/* The substitution autotuner's record for this handle: one line per tuned batch signature
+ * (layer shapes and column width) with the time of every candidate split-K depth and column
+ * chunk and the choice made.  The autotuner runs the first time a signature is solved (set the
+ * environment variable HZ_AUTOTUNE=0 before hz_create to keep the fixed defaults).  The string
+ * stays valid until the next call on the handle. */
+const char* hz_tuning_report(hz_handle* h);
 
 #ifdef __cplusplus
 }

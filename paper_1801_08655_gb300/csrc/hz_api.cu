@@ -6,6 +6,7 @@
 #include <cstring>
 #include <cstdlib>
 #include <new>
+#include <thread>
 
 #include "hz_internal.cuh"
 #include "hz_ctx.cuh"
@@ -86,6 +87,7 @@ void d2h(Ctx& c, void* dst, const void* src, size_t bytes) {
 size_t elem_size(const Ctx& c) { return c.prec == HZ_PREC_FP64 ? sizeof(double2) : sizeof(float2); }
 
 void release_slots(Ctx& c) {
+    c.plans.clear();  // recorded plans point into the slot batches
     free_batches(c);
     for (void* p : c.slot_acc) cudaFree(p);
     for (void* p : c.slot_x) cudaFree(p);
@@ -247,7 +249,7 @@ extern "C" {
 void hz_default_opts(hz_precision prec, hz_solve_opts* o) {
     if (!o) return;
     o->gmres_tol = prec == HZ_PREC_FP64 ? 1e-10 : 1e-7;
-    o->restart = 20;
+    o->restart = 12;
     o->max_iter = 100;
     o->refine_tol = 1e-9;
     o->max_refine = 3;
@@ -297,6 +299,8 @@ hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz
         HZ_CUDA(cudaMemset(c.d_flag, 0, 4 * sizeof(int)));
         // layer partition: physical planes split evenly, earlier layers take the remainder;
         // layer 0 also owns the top PML planes, layer L-1 the bottom ones
+        int leaf = 64;  // nested-dissection leaf size (cells); HZ_LEAF overrides
+        if (const char* e = std::getenv("HZ_LEAF")) leaf = std::max(8, std::atoi(e));
         const int q = nphys / n_layers, rem = nphys % n_layers;
         int start = c.npml;
         std::vector<LayerCoef> coefs;
@@ -316,7 +320,7 @@ hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz
             auto it = shape_of_nz.find(ly.nzl);
             if (it == shape_of_nz.end()) {
                 Shape sh;
-                build_shape(sh, c.nx, c.ny, ly.nzl, 64);
+                build_shape(sh, c.nx, c.ny, ly.nzl, leaf);
                 std::vector<NodeDev> nds;
                 std::vector<long long> foff;
                 std::vector<int> fm;
@@ -359,8 +363,11 @@ hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz
             c.layers.push_back(ly);
         }
         c.d_coefs = dev_copy(coefs);
+        HZ_CUDA(cudaGetDevice(&c.device));
         if (const char* e = std::getenv("HZ_SUBST_TC")) c.use_tc = std::atoi(e) != 0;
         if (const char* e = std::getenv("HZ_TC_KS")) c.tc_ks = std::max(1, std::atoi(e));
+        if (const char* e = std::getenv("HZ_AUTOTUNE")) c.autotune = std::atoi(e) != 0;
+        if (const char* e = std::getenv("HZ_GRAPHS")) c.use_graphs = std::atoi(e) != 0;
         if (const char* e = std::getenv("HZ_TC_MIN_TILES")) c.tc_min_tiles = std::max(1, std::atoi(e));
         HZ_CUDA(cudaDeviceSynchronize());  // uploads complete before any work on the stream
         *out = h;
@@ -457,6 +464,7 @@ hz_status hz_destroy(hz_handle* h) {
     if (c.stream) cudaStreamSynchronize(c.stream);
     else cudaDeviceSynchronize();
     release_slots(c);
+    c.gw.release();
     for (auto& sh : c.shapes) {
         cudaFree(sh.d_nodes); cudaFree(sh.d_pos); cudaFree(sh.d_upd_idx); cudaFree(sh.d_asm); cudaFree(sh.d_emap);
     }
@@ -653,5 +661,41 @@ hz_status hz_profile_end(hz_handle* h, int64_t* calls, double* total_ms, double*
 }
 
 int64_t hz_kernel_launches(void) { return (int64_t)hz::g_launch_count.load(); }
+
+hz_status hz_solve_group(hz_handle* const* hs, int32_t n, const double* const* rhs, const int32_t* R,
+                         double* const* u, const hz_solve_opts* opts, hz_solve_info* const* info,
+                         hz_status* statuses) {
+    if (!hs || n < 1 || !rhs || !R || !u) return HZ_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < i; ++j)
+            if (hs[i] == hs[j] || !hs[i]) return HZ_ERR_ARG;  // a handle is not shared between threads
+    std::vector<hz_status> st(n, HZ_OK);
+    std::vector<std::thread> th;
+    th.reserve(n);
+    for (int i = 0; i < n; ++i) {
+        th.emplace_back([&, i]() {
+            if (cudaSetDevice(hs[i]->ctx.device) != cudaSuccess) {
+                cudaGetLastError();
+                st[i] = HZ_ERR_CUDA;
+                return;
+            }
+            st[i] = hz_solve(hs[i], rhs[i], R[i], u[i], opts, info ? info[i] : nullptr);
+        });
+    }
+    for (auto& t : th) t.join();
+    hz_status worst = HZ_OK;
+    for (int i = 0; i < n; ++i) {
+        if (statuses) statuses[i] = st[i];
+        if (worst == HZ_OK && st[i] != HZ_OK) worst = st[i];
+    }
+    return worst;
+}
+
+const char* hz_tuning_report(hz_handle* h) {
+    if (!h) return "";
+    h->ctx.last_error.clear();
+    for (auto& s : h->ctx.tune_log) h->ctx.last_error += s + "\n";
+    return h->ctx.last_error.c_str();
+}
 
 }  // extern "C"

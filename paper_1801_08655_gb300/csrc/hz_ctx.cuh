@@ -1,6 +1,7 @@
 // Solver context shared by the translation units (the object behind hz_handle).
 #pragma once
 
+#include <functional>
 #include <map>
 #include <memory>
 #include <string>
@@ -30,6 +31,8 @@ struct Batch {
     std::vector<int> layers;
     int H = 0;
     int KS = 1 << 30;                           // max reduction tiles per task (split-K)
+    int CC = 0;                                 // right-hand-side columns per block (0: default)
+    bool tc = false;                            // holds tensor-core task lists (large nodes)
     std::vector<long long> off[4], cnt[4];      // per phase (FA, FB, BA, BB) and level, into d_tasks
     int KS_tc = 1 << 30;                        // split-K of the tensor-core tasks (tiles)
     std::vector<long long> pair_off[4], pair_cnt[4];  // tensor-core tasks: two output tiles each
@@ -44,6 +47,83 @@ struct Batch {
 // Event-timed record of substitution calls (enabled by hz_profile_begin).
 struct ProfRec { cudaEvent_t e0, e1; double bytes, flops; };
 
+// Recorded sequence of stream operations with the device descriptors it owns.  run() issues
+// the operations on a stream; run_graph() captures them once into a CUDA graph and replays it.
+struct Rec {
+    std::vector<std::function<void(cudaStream_t)>> ops;
+    std::vector<void*> owned;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t upload_stream = 0;
+    Rec() = default;
+    Rec(const Rec&) = delete;
+    Rec& operator=(const Rec&) = delete;
+    ~Rec() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (void* p : owned) cudaFree(p);
+    }
+    template <class T> T* up(const std::vector<T>& v) {
+        T* d = nullptr;
+        if (cudaMalloc((void**)&d, std::max<size_t>(1, v.size()) * sizeof(T)) != cudaSuccess) {
+            cudaGetLastError();
+            throw Error{HZ_ERR_OOM, "descriptor upload"};
+        }
+        owned.push_back(d);
+        if (!v.empty()) {
+            HZ_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, upload_stream));
+            HZ_CUDA(cudaStreamSynchronize(upload_stream));
+        }
+        return d;
+    }
+    void add(std::function<void(cudaStream_t)> f) { ops.push_back(std::move(f)); }
+    void run(cudaStream_t st) { for (auto& f : ops) f(st); }
+    void run_graph(cudaStream_t st) {
+        if (!exec) {
+            // capture on a private stream (the legacy default stream cannot be captured); the
+            // instantiated graph is then launched on the caller's stream
+            cudaStream_t cs = nullptr;
+            HZ_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) {
+                cudaStreamDestroy(cs);
+                throw Error{HZ_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e)};
+            }
+            try {
+                run(cs);
+            } catch (...) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(cs, &g);
+                if (g) cudaGraphDestroy(g);
+                cudaStreamDestroy(cs);
+                cudaGetLastError();
+                throw;
+            }
+            e = cudaStreamEndCapture(cs, &graph);
+            cudaStreamDestroy(cs);
+            if (e != cudaSuccess) throw Error{HZ_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e)};
+            HZ_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+        }
+        HZ_CUDA(cudaGraphLaunch(exec, st));
+    }
+};
+
+// Persistent GMRES workspace of a handle (sized for up to cap_R columns).
+struct GmresWork {
+    int cap_R = 0, m = 0;
+    std::vector<void*> bufs;
+    double2 *V = nullptr, *in = nullptr, *out = nullptr, *w2 = nullptr, *tmp = nullptr, *b = nullptr, *xs = nullptr;
+    double2 *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *dots = nullptr, *y = nullptr, *t = nullptr;
+    double *nrm = nullptr, *invb = nullptr, *resid = nullptr, *b0 = nullptr;
+    int *active = nullptr, *kused = nullptr;
+    void release() {
+        for (void* p : bufs) cudaFree(p);
+        bufs.clear();
+        cap_R = 0;
+        m = 0;
+    }
+};
+
 struct Ctx {
     // problem
     int nx = 0, ny = 0, nz = 0;
@@ -51,6 +131,7 @@ struct Ctx {
     int npml = 0, npml_loc = 0, L = 1, K = 0;
     hz_precision prec = HZ_PREC_FP64;
     cudaStream_t stream = 0;
+    int device = 0;
     long long P = 0;     // plane size nx*ny
     long long ntr = 0;   // polarized trace vector length per RHS: 2*K*2*P
     // decomposition and symbolic data
@@ -71,6 +152,13 @@ struct Ctx {
     std::map<std::string, Batch> batches;
     std::string last_error;
     bool prof = false;
+    bool use_graphs = true;   // replay the GMRES matrix-vector product as a captured CUDA graph
+    GmresWork gw;
+    std::map<long long, std::unique_ptr<Rec>> plans;   // matvec plans by column count
+    // autotuner: (shape signature, ldc) -> chosen split-K depth and column chunk
+    bool autotune = true;
+    std::map<std::string, std::pair<int, int>> tuned;
+    std::vector<std::string> tune_log;
     bool use_tc = false;    // tensor-core substitution for complex64 at >= 64 columns (opt-in)
     int tc_ks = 4;          // split-K (factor tiles per block) of small tensor-core batches
     int tc_min_tiles = 3;   // output tiles a node product needs to run on the tensor cores

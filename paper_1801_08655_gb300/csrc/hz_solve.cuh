@@ -13,12 +13,17 @@ int padded_ldc(bool is_double, int ncols);
 
 // Job set with per-level task lists, cached by layer list.
 template <class C> Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols);
+// Build (or fetch) a batch with an explicit split-K depth and column chunk.
+template <class C> Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS, int CC);
+// Autotune the substitution of this batch signature (times candidate split-K depths and column
+// chunks on zeroed slot vectors); a no-op once the signature is tuned or when tuning is off.
+template <class C> void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols);
 void free_batches(Ctx& ctx);
 
 // Forward/backward substitution for every job of the batch on ncols columns of the
 // layers' slot vectors (acc holds the right-hand side in elimination order on entry and
 // is clobbered; x receives the solution).
-template <class C> void substitute(Ctx& ctx, const Batch& b, int ncols);
+template <class C> void substitute(Ctx& ctx, const Batch& b, int ncols, cudaStream_t st);
 
 // Online operators on polarized trace vectors [R][2][K][2][P] (complex128, device).
 template <class C> void op_polarized_rhs(Ctx& ctx, const double2* g, bool scale, int R, double2* fpol);

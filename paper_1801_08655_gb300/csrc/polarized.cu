@@ -425,29 +425,9 @@ __global__ void k_gmres_lsq(GmresState s, int R, int m) {
 }
 
 // ------------------------------------------------------------------------------------------
-// host-side helpers
+// host-side helpers: every operator is recorded into a Rec (descriptors uploaded once, stream
+// operations as closures) so that it can run directly or be replayed as a CUDA graph
 // ------------------------------------------------------------------------------------------
-template <class T> T* upload(const std::vector<T>& v, cudaStream_t st, void*& holder) {
-    T* d = nullptr;
-    HZ_CUDA(cudaMallocAsync((void**)&d, std::max<size_t>(1, v.size()) * sizeof(T), st));
-    if (!v.empty()) HZ_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
-    holder = d;
-    return d;
-}
-
-struct Scratch {
-    std::vector<void*> ptrs;
-    cudaStream_t st;
-    explicit Scratch(cudaStream_t s) : st(s) {}
-    ~Scratch() { for (void* p : ptrs) cudaFreeAsync(p, st); }
-    template <class T> T* up(const std::vector<T>& v) {
-        void* h = nullptr;
-        T* d = upload(v, st, h);
-        ptrs.push_back(h);
-        return d;
-    }
-};
-
 inline const double2* pair_ptr(const double2* base, const Ctx& c, int dir, int j) {
     return base + (long long)dir * c.K * 2 * c.P + (long long)j * 2 * c.P;
 }
@@ -456,11 +436,20 @@ inline double2* pair_ptr(double2* base, const Ctx& c, int dir, int j) {
 }
 
 template <class C>
-void zero_slots(Ctx& ctx, const std::vector<int>& layers, int ldc) {
+void rec_zero_slots(Ctx& ctx, Rec& rec, const std::vector<int>& layers, int ldc) {
     for (int l : layers) {
-        const Shape& sh = ctx.shapes[ctx.layers[l].shape];
-        HZ_CUDA(cudaMemsetAsync(ctx.slot_acc[l], 0, (size_t)sh.N * ldc * sizeof(C), ctx.stream));
+        void* p = ctx.slot_acc[l];
+        const size_t bytes = (size_t)ctx.shapes[ctx.layers[l].shape].N * ldc * sizeof(C);
+        rec.add([p, bytes](cudaStream_t st) { HZ_CUDA(cudaMemsetAsync(p, 0, bytes, st)); });
     }
+}
+
+template <class C>
+void rec_subst(Ctx& ctx, Rec& rec, const std::vector<int>& layers, int ncols) {
+    ensure_tuned<C>(ctx, layers, ncols);  // at record time, before any capture
+    const Batch* b = &get_batch<C>(ctx, layers, ncols);
+    Ctx* cp = &ctx;
+    rec.add([cp, b, ncols](cudaStream_t st) { substitute<C>(*cp, *b, ncols, st); });
 }
 
 // S_top on layer l (source pair of interface l-1) / S_bot on layer l (pair of interface l)
@@ -507,29 +496,40 @@ Extract<C> make_extract(Ctx& ctx, int l, bool bottom, int pl, const std::vector<
 }
 
 template <class C>
-void launch_inject(Ctx& ctx, Scratch& scr, const std::vector<Inject<C>>& v, int R) {
+void rec_inject(Ctx& ctx, Rec& rec, const std::vector<Inject<C>>& v, int R) {
     if (v.empty()) return;
-    Inject<C>* d = scr.up(v);
+    const Inject<C>* d = rec.up(v);
     dim3 grid(cdiv(ctx.P, 256), R, (unsigned)v.size());
-    k_inject<C><<<grid, 256, 0, ctx.stream>>>(d, ctx.d_sx_n, ctx.d_sy_n, 1.0 / (ctx.h * ctx.h), ctx.nx, ctx.ny);
-    HZ_CHECK_LAUNCH();
+    const double2 *sx = ctx.d_sx_n, *sy = ctx.d_sy_n;
+    const double ih2 = 1.0 / (ctx.h * ctx.h);
+    const int nx = ctx.nx, ny = ctx.ny;
+    rec.add([=](cudaStream_t st) {
+        k_inject<C><<<grid, 256, 0, st>>>(d, sx, sy, ih2, nx, ny);
+        HZ_CHECK_LAUNCH();
+    });
 }
 
 template <class C>
-void launch_extract(Ctx& ctx, Scratch& scr, const std::vector<Extract<C>>& v, int R) {
+void rec_extract(Ctx& ctx, Rec& rec, const std::vector<Extract<C>>& v, int R) {
     if (v.empty()) return;
-    Extract<C>* d = scr.up(v);
+    const Extract<C>* d = rec.up(v);
     dim3 grid(cdiv(ctx.P, 256), R, (unsigned)v.size());
-    k_extract<C><<<grid, 256, 0, ctx.stream>>>(d, (int)ctx.P);
-    HZ_CHECK_LAUNCH();
+    const int P = (int)ctx.P;
+    rec.add([=](cudaStream_t st) {
+        k_extract<C><<<grid, 256, 0, st>>>(d, P);
+        HZ_CHECK_LAUNCH();
+    });
 }
 
-void pairs_axpy(Ctx& ctx, double2* y, long long ys, const double2* x, long long xs, double a, const double2* z,
-                long long zs, double b, int zplane, int npairs, int R) {
-    long long n = (long long)npairs * 2 * ctx.P;
+void rec_pairs_axpy(Ctx& ctx, Rec& rec, double2* y, long long ys, const double2* x, long long xs, double a,
+                    const double2* z, long long zs, double b, int zplane, int npairs, int R) {
+    const long long n = (long long)npairs * 2 * ctx.P;
     dim3 grid(cdiv(n, 256), R);
-    k_pairs_axpy<<<grid, 256, 0, ctx.stream>>>(y, ys, x, xs, a, z, zs, b, zplane, npairs, (int)ctx.P);
-    HZ_CHECK_LAUNCH();
+    const int P = (int)ctx.P;
+    rec.add([=](cudaStream_t st) {
+        k_pairs_axpy<<<grid, 256, 0, st>>>(y, ys, x, xs, a, z, zs, b, zplane, npairs, P);
+        HZ_CHECK_LAUNCH();
+    });
 }
 
 std::vector<int> all_layers(const Ctx& ctx) {
@@ -539,8 +539,8 @@ std::vector<int> all_layers(const Ctx& ctx) {
 }
 
 template <class C>
-void volume_sources(Ctx& ctx, Scratch& scr, const std::vector<int>& layers, const double2* g, bool scale, int R,
-                    int ldc) {
+void rec_volume_sources(Ctx& ctx, Rec& rec, const std::vector<int>& layers, const double2* g, bool scale, int R,
+                        int ldc) {
     std::vector<VolIO<C>> io;
     int maxpl = 0;
     for (int l : layers) {
@@ -552,48 +552,40 @@ void volume_sources(Ctx& ctx, Scratch& scr, const std::vector<int>& layers, cons
         io.push_back(q);
         maxpl = std::max(maxpl, ly.hi - ly.lo + 1);
     }
-    VolIO<C>* d = scr.up(io);
+    const VolIO<C>* d = rec.up(io);
     dim3 grid(cdiv(ctx.P, 256), maxpl, (unsigned)io.size());
-    k_volume_source<C><<<grid, 256, 0, ctx.stream>>>(d, g, R, (long long)ctx.nz * ctx.P, ctx.nx, ctx.ny, ctx.d_sx_n,
-                                                     ctx.d_sy_n, ctx.d_sz_n, scale ? 1 : 0);
-    HZ_CHECK_LAUNCH();
+    const long long N3 = (long long)ctx.nz * ctx.P;
+    const int nx = ctx.nx, ny = ctx.ny;
+    const double2 *sx = ctx.d_sx_n, *sy = ctx.d_sy_n, *sz = ctx.d_sz_n;
+    const int sc = scale ? 1 : 0;
+    rec.add([=](cudaStream_t st) {
+        k_volume_source<C><<<grid, 256, 0, st>>>(d, g, R, N3, nx, ny, sx, sy, sz, sc);
+        HZ_CHECK_LAUNCH();
+    });
+}
+
+// run a freshly recorded operator once and release its descriptors
+inline void run_now(Ctx& ctx, Rec& rec) {
+    rec.run(ctx.stream);
+    HZ_CUDA(cudaStreamSynchronize(ctx.stream));
 }
 
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
-// operators
+// operators (recorders)
 // ------------------------------------------------------------------------------------------
 template <class C>
-void op_layer_solve(Ctx& ctx, int ell, const double2* g, int ncols, double2* w) {
-    const bool dbl = sizeof(C) == 16;
-    const int ldc = padded_ldc(dbl, ncols);
-    if (ldc > ctx.slot_cap) throw Error{HZ_ERR_ADMISSION, "too many columns for the layer workspace"};
-    const Layer& ly = ctx.layers[ell];
-    const Shape& sh = ctx.shapes[ly.shape];
-    std::vector<int> one{ell};
-    Batch& b = get_batch<C>(ctx, one, ncols);
-    zero_slots<C>(ctx, one, ldc);
-    dim3 grid(cdiv(sh.N, 256), ncols);
-    k_gather_local<C><<<grid, 256, 0, ctx.stream>>>((C*)ctx.slot_acc[ell], sh.d_pos, ldc, g, sh.N, ncols);
-    HZ_CHECK_LAUNCH();
-    substitute<C>(ctx, b, ncols);
-    k_scatter_local<C><<<grid, 256, 0, ctx.stream>>>((const C*)ctx.slot_x[ell], sh.d_pos, ldc, w, sh.N, ncols);
-    HZ_CHECK_LAUNCH();
-}
-
-template <class C>
-void op_polarized_rhs(Ctx& ctx, const double2* g, bool scale, int R, double2* fpol) {
+void rec_polarized_rhs(Ctx& ctx, Rec& rec, const double2* g, bool scale, int R, double2* fpol) {
     const bool dbl = sizeof(C) == 16;
     const int ldc = padded_ldc(dbl, R);
     if (ldc > ctx.slot_cap) throw Error{HZ_ERR_ADMISSION, "too many columns for the layer workspace"};
-    Scratch scr(ctx.stream);
     auto layers = all_layers(ctx);
-    Batch& b = get_batch<C>(ctx, layers, R);
-    zero_slots<C>(ctx, layers, ldc);
-    volume_sources<C>(ctx, scr, layers, g, scale, R, ldc);
-    substitute<C>(ctx, b, R);
-    HZ_CUDA(cudaMemsetAsync(fpol, 0, (size_t)R * ctx.ntr * sizeof(double2), ctx.stream));
+    rec_zero_slots<C>(ctx, rec, layers, ldc);
+    rec_volume_sources<C>(ctx, rec, layers, g, scale, R, ldc);
+    rec_subst<C>(ctx, rec, layers, R);
+    const size_t bytes = (size_t)R * ctx.ntr * sizeof(double2);
+    rec.add([fpol, bytes](cudaStream_t st) { HZ_CUDA(cudaMemsetAsync(fpol, 0, bytes, st)); });
     std::vector<Extract<C>> ex;
     for (int j = 0; j < ctx.K; ++j)
         for (int pl = 0; pl < 2; ++pl) {
@@ -601,21 +593,20 @@ void op_polarized_rhs(Ctx& ctx, const double2* g, bool scale, int R, double2* fp
             ex.push_back(make_extract<C>(ctx, j, true, pl, {0}, pair_ptr(fpol, ctx, 0, j) + pl * ctx.P, ctx.ntr, ldc, -1.0));
             ex.push_back(make_extract<C>(ctx, j + 1, false, pl, {0}, pair_ptr(fpol, ctx, 1, j) + pl * ctx.P, ctx.ntr, ldc, -1.0));
         }
-    launch_extract<C>(ctx, scr, ex, R);
+    rec_extract<C>(ctx, rec, ex, R);
 }
 
 // y = M_pol x: u_down = D_down x_down + U x_up,  u_up = D_up x_up + L x_down.
 template <class C>
-void op_apply_mpol(Ctx& ctx, const double2* x, int R, double2* y) {
+void rec_apply_mpol(Ctx& ctx, Rec& rec, const double2* x, int R, double2* y) {
     const bool dbl = sizeof(C) == 16;
     const int K = ctx.K, L = ctx.L;
-    Scratch scr(ctx.stream);
     const long long ntr = ctx.ntr;
     // identity terms: u_down_j = -x_down_j - [P plane] x_up_j ; u_up_j = -x_up_j - [Q plane] x_down_j
-    pairs_axpy(ctx, pair_ptr(y, ctx, 0, 0), ntr, pair_ptr(x, ctx, 0, 0), ntr, -1.0, pair_ptr(x, ctx, 1, 0), ntr,
-               -1.0, 0, K, R);
-    pairs_axpy(ctx, pair_ptr(y, ctx, 1, 0), ntr, pair_ptr(x, ctx, 1, 0), ntr, -1.0, pair_ptr(x, ctx, 0, 0), ntr,
-               -1.0, 1, K, R);
+    rec_pairs_axpy(ctx, rec, pair_ptr(y, ctx, 0, 0), ntr, pair_ptr(x, ctx, 0, 0), ntr, -1.0, pair_ptr(x, ctx, 1, 0), ntr,
+                   -1.0, 0, K, R);
+    rec_pairs_axpy(ctx, rec, pair_ptr(y, ctx, 1, 0), ntr, pair_ptr(x, ctx, 1, 0), ntr, -1.0, pair_ptr(x, ctx, 0, 0), ntr,
+                   -1.0, 1, K, R);
     // source blocks: 0 = S_top x_down_{l-1}, 1 = S_bot x_down_l, 2 = S_top x_up_{l-1}, 3 = S_bot x_up_l
     int per_pass = 4;
     while (per_pass > 1 && padded_ldc(dbl, per_pass * R) > ctx.slot_cap) per_pass /= 2;
@@ -625,8 +616,7 @@ void op_apply_mpol(Ctx& ctx, const double2* x, int R, double2* y) {
         const int nbk = per_pass;
         const int ncols = nbk * R;
         const int ldc = padded_ldc(dbl, ncols);
-        Batch& b = get_batch<C>(ctx, layers, ncols);
-        zero_slots<C>(ctx, layers, ldc);
+        rec_zero_slots<C>(ctx, rec, layers, ldc);
         std::vector<Inject<C>> inj;
         int colof[4] = {-1, -1, -1, -1};
         for (int q = 0; q < nbk; ++q) colof[p0 + q] = q * R;
@@ -640,8 +630,8 @@ void op_apply_mpol(Ctx& ctx, const double2* x, int R, double2* y) {
                 if (!top && l <= L - 2)
                     inj.push_back(make_inject<C>(ctx, l, false, pair_ptr(x, ctx, dir, l), ntr, ldc, q * R));
             }
-        launch_inject<C>(ctx, scr, inj, R);
-        substitute<C>(ctx, b, ncols);
+        rec_inject<C>(ctx, rec, inj, R);
+        rec_subst<C>(ctx, rec, layers, ncols);
         std::vector<Extract<C>> ex;
         for (int j = 0; j < K; ++j) {
             // bottom of layer j -> u_down_j: blocks {0 (l>=1), 2 (l>=1), 3}
@@ -660,93 +650,88 @@ void op_apply_mpol(Ctx& ctx, const double2* x, int R, double2* y) {
                     ex.push_back(make_extract<C>(ctx, j + 1, false, pl, ct, pair_ptr(y, ctx, 1, j) + pl * ctx.P, ntr, ldc, 1.0));
             }
         }
-        launch_extract<C>(ctx, scr, ex, R);
+        rec_extract<C>(ctx, rec, ex, R);
     }
 }
 
 // y = P x (Eq. 16): y_down = sweep_down(x_down); s = x_up - L y_down; y_up = sweep_up(s).
 // tmp: one trace vector [R][ntr] of scratch.
 template <class C>
-void op_apply_precond(Ctx& ctx, const double2* x, int R, double2* y, double2* tmp) {
+void rec_apply_precond(Ctx& ctx, Rec& rec, const double2* x, int R, double2* y, double2* tmp) {
     const bool dbl = sizeof(C) == 16;
     const int K = ctx.K, L = ctx.L;
     const long long ntr = ctx.ntr;
     const int ldc = padded_ldc(dbl, R);
     if (ldc > ctx.slot_cap) throw Error{HZ_ERR_ADMISSION, "too many columns for the layer workspace"};
-    Scratch scr(ctx.stream);
     // downward sweep (Algorithm 4)
-    pairs_axpy(ctx, pair_ptr(y, ctx, 0, 0), ntr, pair_ptr(x, ctx, 0, 0), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
+    rec_pairs_axpy(ctx, rec, pair_ptr(y, ctx, 0, 0), ntr, pair_ptr(x, ctx, 0, 0), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
     for (int j = 1; j < K; ++j) {
         std::vector<int> one{j};
-        Batch& b = get_batch<C>(ctx, one, R);
-        zero_slots<C>(ctx, one, ldc);
-        launch_inject<C>(ctx, scr, {make_inject<C>(ctx, j, true, pair_ptr(y, ctx, 0, j - 1), ntr, ldc, 0)}, R);
-        substitute<C>(ctx, b, R);
-        pairs_axpy(ctx, pair_ptr(y, ctx, 0, j), ntr, pair_ptr(x, ctx, 0, j), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
+        rec_zero_slots<C>(ctx, rec, one, ldc);
+        rec_inject<C>(ctx, rec, {make_inject<C>(ctx, j, true, pair_ptr(y, ctx, 0, j - 1), ntr, ldc, 0)}, R);
+        rec_subst<C>(ctx, rec, one, R);
+        rec_pairs_axpy(ctx, rec, pair_ptr(y, ctx, 0, j), ntr, pair_ptr(x, ctx, 0, j), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
         std::vector<Extract<C>> ex;
         for (int pl = 0; pl < 2; ++pl)
             ex.push_back(make_extract<C>(ctx, j, true, pl, {0}, pair_ptr(y, ctx, 0, j) + pl * ctx.P, ntr, ldc, 1.0));
-        launch_extract<C>(ctx, scr, ex, R);
+        rec_extract<C>(ctx, rec, ex, R);
     }
     // upward reflections (Algorithm 6): s_j = x_up_j - ([w]_P, [w]_Q - y_down_j(Q)),
     // w = G^{j+1} (S_top y_down_j + S_bot y_down_{j+1}); s lives in the up half of tmp
     double2* s = tmp;
-    pairs_axpy(ctx, pair_ptr(s, ctx, 1, 0), ntr, pair_ptr(x, ctx, 1, 0), ntr, 1.0, pair_ptr(y, ctx, 0, 0), ntr, 1.0,
-               1, K, R);
+    rec_pairs_axpy(ctx, rec, pair_ptr(s, ctx, 1, 0), ntr, pair_ptr(x, ctx, 1, 0), ntr, 1.0, pair_ptr(y, ctx, 0, 0), ntr,
+                   1.0, 1, K, R);
     {
         std::vector<int> layers;
         for (int l = 1; l < L; ++l) layers.push_back(l);
-        Batch& b = get_batch<C>(ctx, layers, R);
-        zero_slots<C>(ctx, layers, ldc);
+        rec_zero_slots<C>(ctx, rec, layers, ldc);
         std::vector<Inject<C>> inj;
         for (int l = 1; l < L; ++l) {
             inj.push_back(make_inject<C>(ctx, l, true, pair_ptr(y, ctx, 0, l - 1), ntr, ldc, 0));
             if (l <= L - 2) inj.push_back(make_inject<C>(ctx, l, false, pair_ptr(y, ctx, 0, l), ntr, ldc, 0));
         }
-        launch_inject<C>(ctx, scr, inj, R);
-        substitute<C>(ctx, b, R);
+        rec_inject<C>(ctx, rec, inj, R);
+        rec_subst<C>(ctx, rec, layers, R);
         std::vector<Extract<C>> ex;
         for (int j = 0; j < K; ++j)
             for (int pl = 0; pl < 2; ++pl)
                 ex.push_back(make_extract<C>(ctx, j + 1, false, pl, {0}, pair_ptr(s, ctx, 1, j) + pl * ctx.P, ntr, ldc, -1.0));
-        launch_extract<C>(ctx, scr, ex, R);
+        rec_extract<C>(ctx, rec, ex, R);
     }
     // upward sweep (Algorithm 5)
-    pairs_axpy(ctx, pair_ptr(y, ctx, 1, K - 1), ntr, pair_ptr(s, ctx, 1, K - 1), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
+    rec_pairs_axpy(ctx, rec, pair_ptr(y, ctx, 1, K - 1), ntr, pair_ptr(s, ctx, 1, K - 1), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
     for (int j = K - 2; j >= 0; --j) {
         std::vector<int> one{j + 1};
-        Batch& b = get_batch<C>(ctx, one, R);
-        zero_slots<C>(ctx, one, ldc);
-        launch_inject<C>(ctx, scr, {make_inject<C>(ctx, j + 1, false, pair_ptr(y, ctx, 1, j + 1), ntr, ldc, 0)}, R);
-        substitute<C>(ctx, b, R);
-        pairs_axpy(ctx, pair_ptr(y, ctx, 1, j), ntr, pair_ptr(s, ctx, 1, j), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
+        rec_zero_slots<C>(ctx, rec, one, ldc);
+        rec_inject<C>(ctx, rec, {make_inject<C>(ctx, j + 1, false, pair_ptr(y, ctx, 1, j + 1), ntr, ldc, 0)}, R);
+        rec_subst<C>(ctx, rec, one, R);
+        rec_pairs_axpy(ctx, rec, pair_ptr(y, ctx, 1, j), ntr, pair_ptr(s, ctx, 1, j), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
         std::vector<Extract<C>> ex;
         for (int pl = 0; pl < 2; ++pl)
             ex.push_back(make_extract<C>(ctx, j + 1, false, pl, {0}, pair_ptr(y, ctx, 1, j) + pl * ctx.P, ntr, ldc, 1.0));
-        launch_extract<C>(ctx, scr, ex, R);
+        rec_extract<C>(ctx, rec, ex, R);
     }
 }
 
 // u = reconstruction from f and traces t [R][K][2][P] (Algorithm 2, inner solves).
 template <class C>
-void op_reconstruct(Ctx& ctx, const double2* g, bool scale, const double2* t, int R, double2* u, bool accumulate) {
+void rec_reconstruct(Ctx& ctx, Rec& rec, const double2* g, bool scale, const double2* t, int R, double2* u,
+                     bool accumulate) {
     const bool dbl = sizeof(C) == 16;
     const int L = ctx.L;
     const int ldc = padded_ldc(dbl, R);
     if (ldc > ctx.slot_cap) throw Error{HZ_ERR_ADMISSION, "too many columns for the layer workspace"};
-    Scratch scr(ctx.stream);
     auto layers = all_layers(ctx);
-    Batch& b = get_batch<C>(ctx, layers, R);
-    zero_slots<C>(ctx, layers, ldc);
-    volume_sources<C>(ctx, scr, layers, g, scale, R, ldc);
+    rec_zero_slots<C>(ctx, rec, layers, ldc);
+    rec_volume_sources<C>(ctx, rec, layers, g, scale, R, ldc);
     const long long ts = (long long)ctx.K * 2 * ctx.P;
     std::vector<Inject<C>> inj;
     for (int l = 0; l < L; ++l) {
         if (l >= 1) inj.push_back(make_inject<C>(ctx, l, true, t + (long long)(l - 1) * 2 * ctx.P, ts, ldc, 0));
         if (l <= L - 2) inj.push_back(make_inject<C>(ctx, l, false, t + (long long)l * 2 * ctx.P, ts, ldc, 0));
     }
-    launch_inject<C>(ctx, scr, inj, R);
-    substitute<C>(ctx, b, R);
+    rec_inject<C>(ctx, rec, inj, R);
+    rec_subst<C>(ctx, rec, layers, R);
     std::vector<VolIO<C>> io;
     int maxpl = 0;
     for (int l : layers) {
@@ -758,10 +743,77 @@ void op_reconstruct(Ctx& ctx, const double2* g, bool scale, const double2* t, in
         io.push_back(q);
         maxpl = std::max(maxpl, ly.hi - ly.lo + 1);
     }
-    VolIO<C>* d = scr.up(io);
+    const VolIO<C>* d = rec.up(io);
     dim3 grid(cdiv(ctx.P, 256), maxpl, (unsigned)io.size());
-    k_volume_out<C><<<grid, 256, 0, ctx.stream>>>(d, u, R, (long long)ctx.nz * ctx.P, (int)ctx.P, accumulate ? 1 : 0);
-    HZ_CHECK_LAUNCH();
+    const long long N3 = (long long)ctx.nz * ctx.P;
+    const int P = (int)ctx.P, acc = accumulate ? 1 : 0;
+    rec.add([=](cudaStream_t st) {
+        k_volume_out<C><<<grid, 256, 0, st>>>(d, u, R, N3, P, acc);
+        HZ_CHECK_LAUNCH();
+    });
+}
+
+// ------------------------------------------------------------------------------------------
+// one-shot operators (stage entry points)
+// ------------------------------------------------------------------------------------------
+template <class C>
+void op_layer_solve(Ctx& ctx, int ell, const double2* g, int ncols, double2* w) {
+    const bool dbl = sizeof(C) == 16;
+    const int ldc = padded_ldc(dbl, ncols);
+    if (ldc > ctx.slot_cap) throw Error{HZ_ERR_ADMISSION, "too many columns for the layer workspace"};
+    const Layer& ly = ctx.layers[ell];
+    const Shape& sh = ctx.shapes[ly.shape];
+    std::vector<int> one{ell};
+    Rec rec;
+    rec.upload_stream = ctx.stream;
+    rec_zero_slots<C>(ctx, rec, one, ldc);
+    dim3 grid(cdiv(sh.N, 256), ncols);
+    C* acc = (C*)ctx.slot_acc[ell];
+    const C* xv = (const C*)ctx.slot_x[ell];
+    const int* pos = sh.d_pos;
+    const long long N = sh.N;
+    rec.add([=](cudaStream_t st) {
+        k_gather_local<C><<<grid, 256, 0, st>>>(acc, pos, ldc, g, N, ncols);
+        HZ_CHECK_LAUNCH();
+    });
+    rec_subst<C>(ctx, rec, one, ncols);
+    rec.add([=](cudaStream_t st) {
+        k_scatter_local<C><<<grid, 256, 0, st>>>(xv, pos, ldc, w, N, ncols);
+        HZ_CHECK_LAUNCH();
+    });
+    run_now(ctx, rec);
+}
+
+template <class C>
+void op_polarized_rhs(Ctx& ctx, const double2* g, bool scale, int R, double2* fpol) {
+    Rec rec;
+    rec.upload_stream = ctx.stream;
+    rec_polarized_rhs<C>(ctx, rec, g, scale, R, fpol);
+    run_now(ctx, rec);
+}
+
+template <class C>
+void op_apply_mpol(Ctx& ctx, const double2* x, int R, double2* y) {
+    Rec rec;
+    rec.upload_stream = ctx.stream;
+    rec_apply_mpol<C>(ctx, rec, x, R, y);
+    run_now(ctx, rec);
+}
+
+template <class C>
+void op_apply_precond(Ctx& ctx, const double2* x, int R, double2* y, double2* tmp) {
+    Rec rec;
+    rec.upload_stream = ctx.stream;
+    rec_apply_precond<C>(ctx, rec, x, R, y, tmp);
+    run_now(ctx, rec);
+}
+
+template <class C>
+void op_reconstruct(Ctx& ctx, const double2* g, bool scale, const double2* t, int R, double2* u, bool accumulate) {
+    Rec rec;
+    rec.upload_stream = ctx.stream;
+    rec_reconstruct<C>(ctx, rec, g, scale, t, R, u, accumulate);
+    run_now(ctx, rec);
 }
 
 void op_volume_residual(Ctx& ctx, const double2* f, bool scale, const double2* u, int R, double2* r, double* norms) {
@@ -777,7 +829,65 @@ void op_volume_residual(Ctx& ctx, const double2* f, bool scale, const double2* u
 // ------------------------------------------------------------------------------------------
 // GMRES on P M_pol u = P f_pol (Eq. 15), x0 = 0, one Krylov space per column, CGS2.
 // Then traces t = u_down + u_up and the volume reconstruction.  Writes u (not accumulated).
+// The workspace persists in the handle; the matrix-vector product P M_pol (fixed input and
+// output buffers) is recorded once per column count and replayed as a CUDA graph.
 // ------------------------------------------------------------------------------------------
+namespace {
+
+void ensure_gmres_work(Ctx& ctx, int R, int m) {
+    GmresWork& g = ctx.gw;
+    if (g.cap_R >= R && g.m == m) return;
+    g.release();
+    ctx.plans.clear();
+    const long long n = ctx.ntr;
+    const long long vs = (long long)R * n;
+    auto alloc = [&](size_t bytes) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+            cudaGetLastError();
+            g.release();
+            throw Error{HZ_ERR_ADMISSION, "GMRES workspace does not fit in device memory"};
+        }
+        g.bufs.push_back(p);
+        return p;
+    };
+    g.V = (double2*)alloc((size_t)(m + 1) * vs * sizeof(double2));
+    g.in = (double2*)alloc((size_t)vs * sizeof(double2));
+    g.out = (double2*)alloc((size_t)vs * sizeof(double2));
+    g.w2 = (double2*)alloc((size_t)vs * sizeof(double2));
+    g.tmp = (double2*)alloc((size_t)vs * sizeof(double2));
+    g.b = (double2*)alloc((size_t)vs * sizeof(double2));
+    g.xs = (double2*)alloc((size_t)vs * sizeof(double2));
+    g.H = (double2*)alloc((size_t)R * (m + 1) * m * sizeof(double2));
+    g.cs = (double2*)alloc((size_t)R * m * sizeof(double2));
+    g.sn = (double2*)alloc((size_t)R * m * sizeof(double2));
+    g.g = (double2*)alloc((size_t)R * (m + 1) * sizeof(double2));
+    g.dots = (double2*)alloc((size_t)R * (m + 1) * sizeof(double2));
+    g.y = (double2*)alloc((size_t)R * m * sizeof(double2));
+    g.t = (double2*)alloc((size_t)R * ctx.K * 2 * ctx.P * sizeof(double2));
+    g.nrm = (double*)alloc(R * sizeof(double));
+    g.invb = (double*)alloc(R * sizeof(double));
+    g.resid = (double*)alloc(R * sizeof(double));
+    g.b0 = (double*)alloc(R * sizeof(double));
+    g.active = (int*)alloc(R * sizeof(int));
+    g.kused = (int*)alloc(R * sizeof(int));
+    g.cap_R = R;
+    g.m = m;
+}
+
+template <class C>
+Rec& matvec_plan(Ctx& ctx, int R) {
+    auto it = ctx.plans.find(R);
+    if (it != ctx.plans.end()) return *it->second;
+    auto rec = std::make_unique<Rec>();
+    rec->upload_stream = ctx.stream;
+    rec_apply_mpol<C>(ctx, *rec, ctx.gw.in, R, ctx.gw.w2);
+    rec_apply_precond<C>(ctx, *rec, ctx.gw.w2, R, ctx.gw.out, ctx.gw.tmp);
+    return *ctx.plans.emplace(R, std::move(rec)).first->second;
+}
+
+}  // namespace
+
 template <class C>
 void gmres_solve(Ctx& ctx, const double2* g, bool scale, int R, double2* u, const hz_solve_opts& o,
                  hz_solve_info* info) {
@@ -789,130 +899,106 @@ void gmres_solve(Ctx& ctx, const double2* g, bool scale, int R, double2* u, cons
         return;
     }
     const int m = std::max(1, std::min(o.restart, o.max_iter));
+    ensure_gmres_work(ctx, R, m);
+    GmresWork& W = ctx.gw;
     const long long vs = (long long)R * n;  // stride between Krylov vectors
-    std::vector<void*> allocs;
-    auto alloc = [&](size_t bytes) {
-        void* p = nullptr;
-        if (cudaMallocAsync(&p, std::max<size_t>(bytes, 16), st) != cudaSuccess) {
-            cudaGetLastError();
-            for (void* q : allocs) cudaFreeAsync(q, st);
-            allocs.clear();
-            throw Error{HZ_ERR_ADMISSION, "GMRES workspace does not fit in device memory"};
-        }
-        allocs.push_back(p);
-        return p;
-    };
-    double2* V = (double2*)alloc((size_t)(m + 1) * vs * sizeof(double2));
-    double2* w = (double2*)alloc((size_t)vs * sizeof(double2));
-    double2* w2 = (double2*)alloc((size_t)vs * sizeof(double2));
-    double2* tmp = (double2*)alloc((size_t)vs * sizeof(double2));
-    double2* b = (double2*)alloc((size_t)vs * sizeof(double2));
-    double2* xs = (double2*)alloc((size_t)vs * sizeof(double2));
     GmresState s;
-    s.H = (double2*)alloc((size_t)R * (m + 1) * m * sizeof(double2));
-    s.cs_sn = (double2*)alloc((size_t)R * m * sizeof(double2));
-    s.sn = (double2*)alloc((size_t)R * m * sizeof(double2));
-    s.g = (double2*)alloc((size_t)R * (m + 1) * sizeof(double2));
-    s.dots = (double2*)alloc((size_t)R * (m + 1) * sizeof(double2));
-    s.y = (double2*)alloc((size_t)R * m * sizeof(double2));
-    s.nrm = (double*)alloc(R * sizeof(double));
-    s.invb = (double*)alloc(R * sizeof(double));
-    s.resid = (double*)alloc(R * sizeof(double));
-    double* b0 = (double*)alloc(R * sizeof(double));
-    s.active = (int*)alloc(R * sizeof(int));
-    s.kused = (int*)alloc(R * sizeof(int));
+    s.H = W.H; s.cs_sn = W.cs; s.sn = W.sn; s.g = W.g; s.dots = W.dots; s.y = W.y;
+    s.nrm = W.nrm; s.invb = W.invb; s.resid = W.resid; s.active = W.active; s.kused = W.kused;
+    double* b0 = W.b0;
     const long long half = (long long)ctx.K * 2 * ctx.P;
-    double2* t = (double2*)alloc((size_t)R * half * sizeof(double2));
     const int TB = 256;
     const int gblocks = (int)std::min<long long>(1024, std::max<long long>(1, (n + TB - 1) / TB));
     const dim3 gvec(cdiv(n, TB), R);
+    Rec& mv = matvec_plan<C>(ctx, R);
     auto matvec = [&](const double2* in, double2* out) {
-        op_apply_mpol<C>(ctx, in, R, w2);
-        op_apply_precond<C>(ctx, w2, R, out, tmp);
+        HZ_CUDA(cudaMemcpyAsync(W.in, in, (size_t)vs * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        if (ctx.use_graphs && !ctx.prof) mv.run_graph(st);
+        else mv.run(st);
+        if (out != W.out) HZ_CUDA(cudaMemcpyAsync(out, W.out, (size_t)vs * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     };
     auto norms = [&](const double2* v, double* out) {
         HZ_CUDA(cudaMemsetAsync(out, 0, R * sizeof(double), st));
         k_nrm2<<<dim3(gblocks, R), TB, 0, st>>>(v, n, out);
         HZ_CHECK_LAUNCH();
     };
+    std::vector<int> hact(R);
     auto any_active = [&]() {
-        std::vector<int> h(R);
-        HZ_CUDA(cudaMemcpyAsync(h.data(), s.active, R * sizeof(int), cudaMemcpyDeviceToHost, st));
+        HZ_CUDA(cudaMemcpyAsync(hact.data(), s.active, R * sizeof(int), cudaMemcpyDeviceToHost, st));
         HZ_CUDA(cudaStreamSynchronize(st));
-        for (int r = 0; r < R; ++r) if (h[r]) return true;
+        for (int r = 0; r < R; ++r) if (hact[r]) return true;
         return false;
     };
     const double tiny = 1e-300;
     std::vector<double> h_resid(R), h_b0(R);
     int total_it = 0;
-    try {
-        // b = P f_pol ; x = 0
-        op_polarized_rhs<C>(ctx, g, scale, R, w);
-        op_apply_precond<C>(ctx, w, R, b, tmp);
-        HZ_CUDA(cudaMemsetAsync(xs, 0, (size_t)vs * sizeof(double2), st));
-        norms(b, b0);
-        {
-            std::vector<int> ones(R, 1);
-            HZ_CUDA(cudaMemcpyAsync(s.active, ones.data(), R * sizeof(int), cudaMemcpyHostToDevice, st));
-            HZ_CUDA(cudaStreamSynchronize(st));
-        }
-        bool first = true;
-        for (;;) {
-            // residual of the preconditioned system: r0 = b - P M x
-            if (first) {
-                HZ_CUDA(cudaMemcpyAsync(w, b, (size_t)vs * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-            } else {
-                matvec(xs, w);
-                k_lincomb<<<gvec, TB, 0, st>>>(w, n, 1.0, b, n, -1.0, w, n, n);
-                HZ_CHECK_LAUNCH();
-            }
-            first = false;
-            norms(w, s.nrm);
-            k_gmres_start<<<cdiv(R, 128), 128, 0, st>>>(s, R, m, tiny);
-            HZ_CHECK_LAUNCH();
-            k_scale_vec<<<gvec, TB, 0, st>>>(V, w, n, s.invb);
-            HZ_CHECK_LAUNCH();
-            if (!any_active()) break;
-            for (int j = 0; j < m && total_it < o.max_iter; ++j) {
-                matvec(V + (long long)j * vs, w);
-                HZ_CUDA(cudaMemsetAsync(s.dots, 0, (size_t)R * (m + 1) * sizeof(double2), st));
-                for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-                    HZ_CUDA(cudaMemsetAsync(s.y, 0, (size_t)R * m * sizeof(double2), st));
-                    k_mdot<<<dim3(gblocks, R), TB, 0, st>>>(V, vs, w, n, j + 1, s.y, m);
-                    HZ_CHECK_LAUNCH();
-                    k_maxpy<<<gvec, TB, 0, st>>>(V, vs, w, n, j + 1, s.y, m);
-                    HZ_CHECK_LAUNCH();
-                    k_accum_dots<<<cdiv(R * (j + 1), 128), 128, 0, st>>>(s.dots, s.y, R, m, j + 1);
-                    HZ_CHECK_LAUNCH();
-                }
-                norms(w, s.nrm);
-                k_gmres_arnoldi<<<cdiv(R, 128), 128, 0, st>>>(s, R, m, j, 0.0, b0, o.gmres_tol, tiny);
-                HZ_CHECK_LAUNCH();
-                k_scale_vec<<<gvec, TB, 0, st>>>(V + (long long)(j + 1) * vs, w, n, s.invb);
-                HZ_CHECK_LAUNCH();
-                ++total_it;
-                if (!any_active()) break;
-            }
-            // x += V y for this cycle
-            k_gmres_lsq<<<cdiv(R, 128), 128, 0, st>>>(s, R, m);
-            HZ_CHECK_LAUNCH();
-            k_maxpy_plus<<<gvec, TB, 0, st>>>(V, vs, xs, n, m, s.y, m);
-            HZ_CHECK_LAUNCH();
-            if (!any_active() || total_it >= o.max_iter) break;
-            // columns still active restart from their current iterate
-        }
-        HZ_CUDA(cudaMemcpyAsync(h_resid.data(), s.resid, R * sizeof(double), cudaMemcpyDeviceToHost, st));
-        HZ_CUDA(cudaMemcpyAsync(h_b0.data(), b0, R * sizeof(double), cudaMemcpyDeviceToHost, st));
-        // traces t = x_down + x_up, laid out [R][K][2][P]
-        k_lincomb<<<dim3(cdiv(half, TB), R), TB, 0, st>>>(t, half, 1.0, xs, n, 1.0, xs + half, n, half);
-        HZ_CHECK_LAUNCH();
-        op_reconstruct<C>(ctx, g, scale, t, R, u, false);
-        HZ_CUDA(cudaStreamSynchronize(st));
-    } catch (...) {
-        for (void* p : allocs) cudaFreeAsync(p, st);
-        throw;
+    // b = P f_pol ; x = 0
+    {
+        Rec rec;
+        rec.upload_stream = st;
+        rec_polarized_rhs<C>(ctx, rec, g, scale, R, W.w2);
+        rec_apply_precond<C>(ctx, rec, W.w2, R, W.b, W.tmp);
+        run_now(ctx, rec);
     }
-    for (void* p : allocs) cudaFreeAsync(p, st);
+    HZ_CUDA(cudaMemsetAsync(W.xs, 0, (size_t)vs * sizeof(double2), st));
+    norms(W.b, b0);
+    {
+        std::vector<int> ones(R, 1);
+        HZ_CUDA(cudaMemcpyAsync(s.active, ones.data(), R * sizeof(int), cudaMemcpyHostToDevice, st));
+        HZ_CUDA(cudaStreamSynchronize(st));
+    }
+    double2* w = W.out;  // the matvec writes its result here
+    bool first = true;
+    for (;;) {
+        // residual of the preconditioned system: r0 = b - P M x
+        if (first) {
+            HZ_CUDA(cudaMemcpyAsync(w, W.b, (size_t)vs * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        } else {
+            matvec(W.xs, w);
+            k_lincomb<<<gvec, TB, 0, st>>>(w, n, 1.0, W.b, n, -1.0, w, n, n);
+            HZ_CHECK_LAUNCH();
+        }
+        first = false;
+        norms(w, s.nrm);
+        k_gmres_start<<<cdiv(R, 128), 128, 0, st>>>(s, R, m, tiny);
+        HZ_CHECK_LAUNCH();
+        k_scale_vec<<<gvec, TB, 0, st>>>(W.V, w, n, s.invb);
+        HZ_CHECK_LAUNCH();
+        if (!any_active()) break;
+        for (int j = 0; j < m && total_it < o.max_iter; ++j) {
+            matvec(W.V + (long long)j * vs, w);
+            HZ_CUDA(cudaMemsetAsync(s.dots, 0, (size_t)R * (m + 1) * sizeof(double2), st));
+            for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+                HZ_CUDA(cudaMemsetAsync(s.y, 0, (size_t)R * m * sizeof(double2), st));
+                k_mdot<<<dim3(gblocks, R), TB, 0, st>>>(W.V, vs, w, n, j + 1, s.y, m);
+                HZ_CHECK_LAUNCH();
+                k_maxpy<<<gvec, TB, 0, st>>>(W.V, vs, w, n, j + 1, s.y, m);
+                HZ_CHECK_LAUNCH();
+                k_accum_dots<<<cdiv(R * (j + 1), 128), 128, 0, st>>>(s.dots, s.y, R, m, j + 1);
+                HZ_CHECK_LAUNCH();
+            }
+            norms(w, s.nrm);
+            k_gmres_arnoldi<<<cdiv(R, 128), 128, 0, st>>>(s, R, m, j, 0.0, b0, o.gmres_tol, tiny);
+            HZ_CHECK_LAUNCH();
+            k_scale_vec<<<gvec, TB, 0, st>>>(W.V + (long long)(j + 1) * vs, w, n, s.invb);
+            HZ_CHECK_LAUNCH();
+            ++total_it;
+            if (!any_active()) break;
+        }
+        // x += V y for this cycle
+        k_gmres_lsq<<<cdiv(R, 128), 128, 0, st>>>(s, R, m);
+        HZ_CHECK_LAUNCH();
+        k_maxpy_plus<<<gvec, TB, 0, st>>>(W.V, vs, W.xs, n, m, s.y, m);
+        HZ_CHECK_LAUNCH();
+        if (!any_active() || total_it >= o.max_iter) break;
+        // columns still active restart from their current iterate
+    }
+    HZ_CUDA(cudaMemcpyAsync(h_resid.data(), s.resid, R * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HZ_CUDA(cudaMemcpyAsync(h_b0.data(), b0, R * sizeof(double), cudaMemcpyDeviceToHost, st));
+    // traces t = x_down + x_up, laid out [R][K][2][P]
+    k_lincomb<<<dim3(cdiv(half, TB), R), TB, 0, st>>>(W.t, half, 1.0, W.xs, n, 1.0, W.xs + half, n, half);
+    HZ_CHECK_LAUNCH();
+    op_reconstruct<C>(ctx, g, scale, W.t, R, u, false);
     HZ_CUDA(cudaStreamSynchronize(st));
     if (info) {
         for (int r = 0; r < R; ++r) {

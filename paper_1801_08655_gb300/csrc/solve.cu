@@ -166,6 +166,131 @@ __global__ void __launch_bounds__(256) k_subst(const Task* __restrict__ tasks,
     }
 }
 
+// 64-column variant for complex64: each thread owns a 2-row x 4-column register tile, fed by
+// three 16-byte shared loads per 8 complex MACs.  The factor tile is kept as [k][row] in shared
+// memory (rows padded to 34 complex, so every row pair is one aligned 16-byte load), transposed
+// on the way in for the transposed phases.
+template <int MODE>
+__global__ void __launch_bounds__(256, 4) k_subst64(const Task* __restrict__ tasks,
+                                                    const JobDev<float2>* __restrict__ jobs, int ldc, int nchunks,
+                                                    int KS) {
+    constexpr int CC = 64;
+    constexpr int MS = 34;                       // padded row length (complex) of the [k][row] tile
+    __shared__ __align__(16) float2 Ms[TILE][MS];
+    __shared__ __align__(16) float2 Xs[TILE][CC];
+
+    const int chunk = blockIdx.x % nchunks;
+    const Task tk = tasks[blockIdx.x / nchunks];
+    const JobDev<float2> jb = jobs[tk.job];
+    const NodeDev nd = jb.nodes[tk.node];
+    const int t = threadIdx.x;
+    const int rp = t & 15, cq = t >> 4;          // rows 2rp, 2rp+1; columns 4cq .. 4cq+3
+    const int col0 = chunk * CC;
+
+    int kend;
+    if (MODE == FA) kend = tk.tile + 1;
+    else if (MODE == FB) kend = nd.own_t;
+    else if (MODE == BA) kend = nd.upd_t;
+    else kend = nd.own_t;
+    const int kt0 = tk.pad_;
+    const int kt1 = min(kend, kt0 + KS);
+    const float2* vec = (MODE == FA || MODE == BB) ? jb.acc : jb.x;
+    const int* upd = jb.upd_idx + nd.upd_off;
+
+    float2 acc[2][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+
+    auto mat_ptr = [&](int kt) -> const float2* {
+        if (MODE == FA) return jb.fac + (nd.linv_off + tri_idx(tk.tile, kt)) * TILE2;
+        if (MODE == FB) return jb.fac + (nd.l21_off + (long long)tk.tile * nd.own_t + kt) * TILE2;
+        if (MODE == BA) return jb.fac + (nd.l21_off + (long long)kt * nd.own_t + tk.tile) * TILE2;
+        return jb.fac + (nd.linv_off + tri_idx(kt, tk.tile)) * TILE2;
+    };
+    float2 pm[4], px[8];
+    auto fetch = [&](int kt) {
+        const float2* mt = mat_ptr(kt);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) pm[i] = mt[t + i * 256];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int e = t + i * 256;
+            const int k = e >> 6, c = e & 63;
+            const int r = kt * TILE + k;
+            float2 v = make_float2(0.f, 0.f);
+            if (MODE == BA) {
+                if (r < nd.nupd) v = vec[(long long)upd[r] * ldc + col0 + c];
+            } else {
+                if (r < nd.nown) v = vec[(long long)(nd.own0 + r) * ldc + col0 + c];
+            }
+            px[i] = v;
+        }
+    };
+    if (kt0 < kt1) fetch(kt0);
+    for (int kt = kt0; kt < kt1; ++kt) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int e = t + i * 256;           // stored element (row e % 32, column e / 32)
+            if (MODE == FA || MODE == FB) Ms[e >> 5][e & 31] = pm[i];   // A(row, k) = stored(row, k)
+            else Ms[e & 31][e >> 5] = pm[i];                              // A(row, k) = stored(k, row)
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int e = t + i * 256;
+            Xs[e >> 6][e & 63] = px[i];
+        }
+        __syncthreads();
+        if (kt + 1 < kt1) fetch(kt + 1);
+#pragma unroll 8
+        for (int k = 0; k < TILE; ++k) {
+            const float4 a2 = *(const float4*)&Ms[k][2 * rp];
+            const float4 x01 = *(const float4*)&Xs[k][4 * cq];
+            const float4 x23 = *(const float4*)&Xs[k][4 * cq + 2];
+            const float2 a0 = make_float2(a2.x, a2.y), a1 = make_float2(a2.z, a2.w);
+            const float2 xs[4] = {make_float2(x01.x, x01.y), make_float2(x01.z, x01.w),
+                                  make_float2(x23.x, x23.y), make_float2(x23.z, x23.w)};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                cfma(acc[0][j], a0, xs[j]);
+                cfma(acc[1][j], a1, xs[j]);
+            }
+        }
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int row = tk.tile * TILE + 2 * rp + i;
+        const int col = col0 + 4 * cq;
+        if (MODE == FB) {
+            if (row >= nd.nupd) continue;
+            float2* dst = jb.acc + (long long)upd[row] * ldc + col;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) atomic_sub(dst + j, acc[i][j]);
+            continue;
+        }
+        if (row >= nd.nown) continue;
+        const long long e = (long long)(nd.own0 + row) * ldc + col;
+        if (MODE == FA || MODE == BB) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) atomic_add(jb.x + e + j, acc[i][j]);
+        } else {
+            if (kt0 == 0) {
+                const float2 di = jb.dinv[nd.own0 + row];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc[i][j] = csub(acc[i][j], cmul(di, jb.x[e + j]));
+                    jb.x[e + j] = make_float2(0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) atomic_sub(jb.acc + e + j, acc[i][j]);
+        }
+    }
+}
+
 template <class C, int CC>
 void launch_level(const Batch& b, int h, int mode, int ldc, cudaStream_t st) {
     const int nchunks = ldc / CC;
@@ -174,11 +299,21 @@ void launch_level(const Batch& b, int h, int mode, int ldc, cudaStream_t st) {
     const Task* tasks = b.d_tasks + off;
     const JobDev<C>* jobs = (const JobDev<C>*)b.d_jobs;
     dim3 grid((unsigned)(n * nchunks));
-    switch (mode) {
-        case FA: k_subst<C, CC, FA><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks, b.KS); break;
-        case FB: k_subst<C, CC, FB><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks, b.KS); break;
-        case BA: k_subst<C, CC, BA><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks, b.KS); break;
-        default: k_subst<C, CC, BB><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks, b.KS); break;
+    if constexpr (CC == 64 && sizeof(C) == 8) {
+        const JobDev<float2>* j64 = (const JobDev<float2>*)b.d_jobs;
+        switch (mode) {
+            case FA: k_subst64<FA><<<grid, 256, 0, st>>>(tasks, j64, ldc, nchunks, b.KS); break;
+            case FB: k_subst64<FB><<<grid, 256, 0, st>>>(tasks, j64, ldc, nchunks, b.KS); break;
+            case BA: k_subst64<BA><<<grid, 256, 0, st>>>(tasks, j64, ldc, nchunks, b.KS); break;
+            default: k_subst64<BB><<<grid, 256, 0, st>>>(tasks, j64, ldc, nchunks, b.KS); break;
+        }
+    } else {
+        switch (mode) {
+            case FA: k_subst<C, CC, FA><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks, b.KS); break;
+            case FB: k_subst<C, CC, FB><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks, b.KS); break;
+            case BA: k_subst<C, CC, BA><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks, b.KS); break;
+            default: k_subst<C, CC, BB><<<grid, 256, 0, st>>>(tasks, jobs, ldc, nchunks, b.KS); break;
+        }
     }
     HZ_CHECK_LAUNCH();
 }
@@ -224,26 +359,25 @@ int padded_ldc(bool is_double, int ncols) {
 }
 
 template <class C>
-void substitute(Ctx& ctx, const Batch& b, int ncols) {
+void substitute(Ctx& ctx, const Batch& b, int ncols, cudaStream_t st) {
     const bool dbl = sizeof(C) == 16;
-    const int cc = chunk_cols(dbl, ncols);
     const int ldc = padded_ldc(dbl, ncols);
-    cudaStream_t st = ctx.stream;
+    const int cc = (b.CC > 0 && ldc % b.CC == 0) ? b.CC : chunk_cols(dbl, ncols);
     ProfRec rec{};
     if (ctx.prof) {
         HZ_CUDA(cudaEventCreate(&rec.e0));
         HZ_CUDA(cudaEventCreate(&rec.e1));
         HZ_CUDA(cudaEventRecord(rec.e0, st));
     }
-    const bool tc = (sizeof(C) == 8) && ctx.use_tc && tc_columns(ldc) > 0;
+    const bool tc = b.tc;
     int* flag = ctx.d_flag + 1;
     switch (cc) {
-        case 1: run_batch<C, 1>(b, ldc, false, flag, st); break;
-        case 2: run_batch<C, 2>(b, ldc, false, flag, st); break;
-        case 4: run_batch<C, 4>(b, ldc, false, flag, st); break;
-        case 8: run_batch<C, 8>(b, ldc, false, flag, st); break;
-        case 16: run_batch<C, 16>(b, ldc, false, flag, st); break;
-        case 32: run_batch<C, 32>(b, ldc, false, flag, st); break;
+        case 1: run_batch<C, 1>(b, ldc, tc, flag, st); break;
+        case 2: run_batch<C, 2>(b, ldc, tc, flag, st); break;
+        case 4: run_batch<C, 4>(b, ldc, tc, flag, st); break;
+        case 8: run_batch<C, 8>(b, ldc, tc, flag, st); break;
+        case 16: run_batch<C, 16>(b, ldc, tc, flag, st); break;
+        case 32: run_batch<C, 32>(b, ldc, tc, flag, st); break;
         default:
             if constexpr (sizeof(C) == 8) run_batch<C, 64>(b, ldc, tc, flag, st);
             else throw Error{HZ_ERR_ARG, "chunk width"};
@@ -264,21 +398,83 @@ static bool tc_node(int mode, const Node& nd, int min_tiles) {
     return out_t >= min_tiles && red_t >= 2;
 }
 
+static std::string tune_key(const Ctx& ctx, const std::vector<int>& layers, int ldc, bool tc) {
+    std::vector<int> shapes;
+    for (int l : layers) shapes.push_back(ctx.layers[l].shape);
+    std::sort(shapes.begin(), shapes.end());
+    std::string key = "n" + std::to_string(ldc) + (tc ? "tc" : "") + ":";
+    for (int s : shapes) key += std::to_string(s) + ",";
+    return key;
+}
+
 template <class C>
 Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols) {
-    // split the reductions when the batch alone cannot fill the GPU (few layers, few chunks)
     const bool dbl = sizeof(C) == 16;
     const int ldc = padded_ldc(dbl, ncols);
-    const int nchunks = ldc / chunk_cols(dbl, ncols);
     const bool tc = !dbl && ctx.use_tc && tc_columns(ldc) > 0;
+    auto it = ctx.tuned.find(tune_key(ctx, layers, ldc, tc));
+    if (it != ctx.tuned.end()) return get_batch_cfg<C>(ctx, layers, ncols, it->second.first, it->second.second);
+    // default: split the reductions when the batch alone cannot fill the GPU
+    const int nchunks = ldc / chunk_cols(dbl, ncols);
     const int KS = ((long long)layers.size() * nchunks >= 64) ? (1 << 30) : 8;
-    std::string key = "KS" + std::to_string(KS) + "n" + std::to_string(ldc) + (tc ? "tc" : "") + ":";
+    return get_batch_cfg<C>(ctx, layers, ncols, KS, 0);
+}
+
+template <class C>
+void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols) {
+    const bool dbl = sizeof(C) == 16;
+    const int ldc = padded_ldc(dbl, ncols);
+    const bool tc = !dbl && ctx.use_tc && tc_columns(ldc) > 0;
+    const std::string key = tune_key(ctx, layers, ldc, tc);
+    if (!ctx.autotune || ctx.tuned.count(key)) return;
+    const int cc0 = chunk_cols(dbl, ncols);
+    std::vector<int> ccs{cc0};
+    if (cc0 >= 16 && ldc % (cc0 / 2) == 0) ccs.push_back(cc0 / 2);
+    const int kss[] = {4, 8, 16, 1 << 30};
+    cudaEvent_t e0, e1;
+    HZ_CUDA(cudaEventCreate(&e0));
+    HZ_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    std::pair<int, int> choice{1 << 30, cc0};
+    const bool prof = ctx.prof;
+    ctx.prof = false;
+    std::string log = key + " ->";
+    for (int cc : ccs)
+        for (int ks : kss) {
+            Batch& b = get_batch_cfg<C>(ctx, layers, ncols, ks, cc);
+            for (size_t j = 0; j < b.vec_ptrs.size(); ++j)
+                HZ_CUDA(cudaMemsetAsync(b.vec_ptrs[j].first, 0, (size_t)b.vec_rows[j] * ldc * sizeof(C), ctx.stream));
+            substitute<C>(ctx, b, ncols, ctx.stream);  // warm-up
+            HZ_CUDA(cudaEventRecord(e0, ctx.stream));
+            substitute<C>(ctx, b, ncols, ctx.stream);
+            HZ_CUDA(cudaEventRecord(e1, ctx.stream));
+            HZ_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            HZ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            log += " (KS " + std::to_string(ks > 1000 ? 0 : ks) + ", CC " + std::to_string(cc) + ") " + std::to_string(ms) + " ms;";
+            if (ms < best) { best = ms; choice = {ks, cc}; }
+        }
+    ctx.prof = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx.tuned[key] = choice;
+    ctx.tune_log.push_back(log);
+}
+
+template <class C>
+Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS, int CC) {
+    const bool dbl = sizeof(C) == 16;
+    const int ldc = padded_ldc(dbl, ncols);
+    const bool tc = !dbl && ctx.use_tc && tc_columns(ldc) > 0;
+    std::string key = "KS" + std::to_string(KS) + "C" + std::to_string(CC) + "n" + std::to_string(ldc) + (tc ? "tc" : "") + ":";
     for (int l : layers) key += std::to_string(l) + ",";
     auto it = ctx.batches.find(key);
     if (it != ctx.batches.end()) return it->second;
     Batch b;
     b.layers = layers;
     b.KS = KS;
+    b.CC = CC;
+    b.tc = tc;
     const int nchunks_tc = tc ? ldc / tc_columns(ldc) : 1;
     b.KS_tc = ((long long)layers.size() * nchunks_tc >= 32) ? (1 << 30) : ctx.tc_ks;
     int H = 0;
@@ -372,9 +568,13 @@ void free_batches(Ctx& ctx) {
     ctx.batches.clear();
 }
 
-template void substitute<float2>(Ctx&, const Batch&, int);
-template void substitute<double2>(Ctx&, const Batch&, int);
+template void substitute<float2>(Ctx&, const Batch&, int, cudaStream_t);
+template void substitute<double2>(Ctx&, const Batch&, int, cudaStream_t);
 template Batch& get_batch<float2>(Ctx&, const std::vector<int>&, int);
 template Batch& get_batch<double2>(Ctx&, const std::vector<int>&, int);
+template Batch& get_batch_cfg<float2>(Ctx&, const std::vector<int>&, int, int, int);
+template Batch& get_batch_cfg<double2>(Ctx&, const std::vector<int>&, int, int, int);
+template void ensure_tuned<float2>(Ctx&, const std::vector<int>&, int);
+template void ensure_tuned<double2>(Ctx&, const std::vector<int>&, int);
 
 }  // namespace hz

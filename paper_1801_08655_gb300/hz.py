@@ -28,6 +28,7 @@ EXPORTED = [
     "hz_layer_info", "hz_factor_stats", "hz_layer_solve_cost", "hz_layer_solve", "hz_polarized_rhs",
     "hz_apply_mpol", "hz_apply_precond", "hz_reconstruct", "hz_volume_residual",
     "hz_profile_begin", "hz_profile_end", "hz_kernel_launches", "hz_volume_residual_noalloc",
+    "hz_tuning_report", "hz_solve_group",
 ]
 
 
@@ -89,10 +90,13 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.hz_profile_begin.argtypes = [VP]
     lib.hz_profile_end.argtypes = [VP, P(ct.c_int64), P(D), P(D), P(D)]
     lib.hz_kernel_launches.argtypes = []
+    lib.hz_tuning_report.argtypes = [VP]
+    lib.hz_solve_group.argtypes = [P(VP), I32, P(VP), P(I32), P(VP), P(SolveOpts), P(VP), P(ct.c_int)]
     for name in EXPORTED:
-        if name not in ("hz_default_opts", "hz_last_error", "hz_kernel_launches"):
+        if name not in ("hz_default_opts", "hz_last_error", "hz_kernel_launches", "hz_tuning_report"):
             getattr(lib, name).restype = ct.c_int
     lib.hz_kernel_launches.restype = ct.c_int64
+    lib.hz_tuning_report.restype = ct.c_char_p
     _lib = lib
     return lib
 
@@ -242,6 +246,9 @@ class Solver:
         self._check(self.lib.hz_volume_residual_noalloc(self.h, _ptr(rhs), _ptr(u), R, _ptr(r), rel))
         return list(rel)
 
+    def tuning_report(self) -> str:
+        return self.lib.hz_tuning_report(self.h).decode()
+
     def profile_begin(self):
         self._check(self.lib.hz_profile_begin(self.h))
 
@@ -257,6 +264,30 @@ class Solver:
         rel = (ct.c_double * R)()
         self._check(self.lib.hz_volume_residual(self.h, _ptr(rhs), _ptr(u), R, _ptr(r), rel))
         return list(rel), r
+
+
+def solve_group(solvers, rhs_list, opts: Optional[SolveOpts] = None, allow_noconv: bool = False):
+    """Solve several factored problems at once (hz_solve_group): rhs_list[i] is a complex128
+    CUDA tensor (R_i, nz_i, ny_i, nx_i) for solvers[i].  Returns ([u_i], [[SolveInfo]_i], [status_i])."""
+    import torch
+    lib = load()
+    n = len(solvers)
+    us = [torch.empty_like(r) for r in rhs_list]
+    infos = [(SolveInfo * r.shape[0])() for r in rhs_list]
+    hs = (ct.c_void_p * n)(*[s.h.value for s in solvers])
+    rp = (ct.c_void_p * n)(*[_ptr(r) for r in rhs_list])
+    up = (ct.c_void_p * n)(*[_ptr(u) for u in us])
+    Rs = (ct.c_int32 * n)(*[r.shape[0] for r in rhs_list])
+    ip = (ct.c_void_p * n)(*[ct.addressof(i) for i in infos])
+    sts = (ct.c_int * n)()
+    for r in rhs_list:
+        assert r.is_cuda and r.dtype == torch.complex128 and r.is_contiguous()
+    st = lib.hz_solve_group(hs, n, rp, Rs, up, ct.byref(opts) if opts else None, ip, sts)
+    ok = (HZ_OK, HZ_ERR_NO_CONVERGENCE) if allow_noconv else (HZ_OK,)
+    if st not in ok:
+        bad = [i for i in range(n) if sts[i] not in ok]
+        raise HzError(st, f"member {bad[0]}: " + lib.hz_last_error(solvers[bad[0]].h).decode())
+    return us, [list(i) for i in infos], list(sts)
 
 
 def kernel_launches() -> int:

@@ -28,7 +28,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_default_options():
     o = hz.default_opts("fp64")
-    assert o.gmres_tol == 1e-10 and o.restart == 20
+    assert o.gmres_tol == 1e-10 and o.restart == 12
     o = hz.default_opts("mixed")
     assert o.gmres_tol == 1e-7 and o.max_refine == 3
 
