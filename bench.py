@@ -391,6 +391,61 @@ def run_batched(args):
         s.close()
 
 
+def run_serving(args):
+    """Serving workload: 160^3 smooth random medium (PML 10, 20 layers), factors resident for
+    three frequencies (8, 10, 12 points per wavelength at c = 1.5), a seeded Poisson request
+    stream, each request R ~ U{1..rmax} surface point sources at one frequency; continuous
+    batching with admission by free device memory.  Reports p50/p99 latency and solves/s."""
+    import torch
+    from paper_1801_08655_gb300 import build, hz, serving, workloads as W
+    torch.cuda.set_device(0)
+    build.build()
+    m, omegas = W.config(5)
+    n, p, L = 160, 10, 20
+    opts = hz.default_opts("mixed")
+    opts.gmres_tol = args.gmres_tol
+    opts.refine_tol = args.refine_tol
+    opts.restart = 6
+    rec = W.point_sources_plane_grid(n, p, p + 2, 8, 8)
+    recv = (rec[:, 0] * n + rec[:, 1]) * n + rec[:, 2]
+    t0 = time.perf_counter()
+    srv = serving.Server(m, omegas, p, W.pml_constant(4.5), L, npml_local=args.npml_local, precision="mixed",
+                         max_cols=args.max_cols, max_workers=2, opts=opts, receivers=recv)
+    factor_s = time.perf_counter() - t0
+    # calibrate the saturated throughput with one full batch at the middle frequency
+    grid = W.point_sources_plane_grid(n, p, p + 2, 16, 16)
+    cal = [serving.Request(-1, 1, grid[:args.max_cols], 0.0)]
+    tcal = srv.serve(cal, realtime=False)
+    cols_per_s = args.max_cols / tcal * len(omegas)
+    reqs_all = W.serving_requests(n, p, args.requests, 1.0, len(omegas), seed=1801 + 50)
+    mean_R = np.mean([min(len(s), args.rmax) for _, _, s in reqs_all])
+    rate = 0.8 * cols_per_s / mean_R
+    rng = np.random.default_rng(1801 + 51)
+    reqs, t = [], 0.0
+    for i, (_, w, src) in enumerate(reqs_all):
+        t += rng.exponential(1.0 / rate)
+        reqs.append(serving.Request(i, w, src[:args.rmax], t))
+    launches0 = hz.kernel_launches()
+    wall = srv.serve(reqs)
+    launches = hz.kernel_launches() - launches0
+    st = serving.latency_stats(reqs)
+    total = sum(r.R for r in reqs)
+    line = {
+        "metric": "serving: online solves/s and p50/p99 request latency (160^3, 3 resident frequencies)",
+        "value": total / wall, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64/f64", "data": "synthetic",
+        "config": {"workload": f"160^3 smooth random, PML 10, 20 layers (local pads {args.npml_local}), "
+                               f"3 frequencies, {args.requests} Poisson requests, R ~ U{{1..{args.rmax}}}",
+                   "max_cols": args.max_cols, "arrival_rate_per_s": rate},
+        "latency": st, "batches": srv.batches, "max_requests_per_batch": srv.max_requests_per_batch,
+        "admission": srv.admission_log, "errors": srv.errors, "factor_s": factor_s, "gpu_launches": launches,
+        "calibration_s_per_batch": tcal,
+    }
+    print(json.dumps(line), flush=True)
+    srv.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -398,9 +453,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--rhs", type=int, default=0, help="right-hand sides per step (default: the workload's R)")
-    ap.add_argument("--config", type=int, default=3, choices=[2, 3, 4],
+    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--rmax", type=int, default=64)
+    ap.add_argument("--max-cols", type=int, default=32)
+    ap.add_argument("--npml-local", type=int, default=5)
+    ap.add_argument("--config", type=int, default=3, choices=[2, 3, 4, 5],
                     help="3: 128^3 layered+block, R=128 (the headline workload); 2: 64^3 smooth, R=16; "
-                         "4: six uneven problems solved as one batch")
+                         "4: six uneven problems solved as one batch; 5: serving 160^3, 3 frequencies")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--fp64-rhs", type=int, default=4)
     ap.add_argument("--no-cpu", action="store_true")
@@ -411,6 +470,8 @@ def main():
         run_reference(args)
     elif args.config == 4:
         run_batched(args)
+    elif args.config == 5:
+        run_serving(args)
     else:
         run_ours(args)
 

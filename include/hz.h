@@ -148,7 +148,16 @@ hz_status hz_solve_group(hz_handle* const* hs, int32_t n, const double* const* r
 hz_status hz_solve_host(hz_handle* h, const double* rhs_host, int32_t R, double* u_host,
                         const hz_solve_opts* opts, hz_solve_info* info);
 
-/* hz_destroy -- frees every device and host buffer of the handle (NULL is allowed). */
+/*
+ * hz_create_shared -- a second handle on an already factored problem: it borrows src's
+ * resident factors and problem data (read-only) and gets its own solve workspaces, error flags
+ * and stream, so that several solves of the same (model, omega) can run at once (one host
+ * thread per handle).  src must stay alive until every handle created from it is destroyed.
+ * Errors: HZ_ERR_ARG, HZ_ERR_STATE (src not factored), HZ_ERR_OOM.
+ */
+hz_status hz_create_shared(hz_handle* src, void* stream, hz_handle** out);
+
+/* hz_destroy -- frees every device and host buffer the handle owns (NULL is allowed). */
 hz_status hz_destroy(hz_handle* h);
 
 /* One-line description of the last failure on this handle ("" if none); the string

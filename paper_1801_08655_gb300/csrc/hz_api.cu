@@ -465,17 +465,61 @@ hz_status hz_destroy(hz_handle* h) {
     else cudaDeviceSynchronize();
     release_slots(c);
     c.gw.release();
-    for (auto& sh : c.shapes) {
-        cudaFree(sh.d_nodes); cudaFree(sh.d_pos); cudaFree(sh.d_upd_idx); cudaFree(sh.d_asm); cudaFree(sh.d_emap);
+    cudaFree(c.d_flag);
+    if (c.owns_shared) {
+        for (auto& sh : c.shapes) {
+            cudaFree(sh.d_nodes); cudaFree(sh.d_pos); cudaFree(sh.d_upd_idx); cudaFree(sh.d_asm); cudaFree(sh.d_emap);
+        }
+        for (auto& ly : c.layers) {
+            cudaFree(ly.d_sz_n); cudaFree(ly.d_isz_h); cudaFree(ly.d_m); cudaFree(ly.d_fac); cudaFree(ly.d_dinv);
+        }
+        cudaFree(c.d_coefs);
+        cudaFree(c.d_sx_n); cudaFree(c.d_isx_h); cudaFree(c.d_sy_n); cudaFree(c.d_isy_h);
+        cudaFree(c.d_sz_n); cudaFree(c.d_isz_h); cudaFree(c.d_m);
     }
-    for (auto& ly : c.layers) {
-        cudaFree(ly.d_sz_n); cudaFree(ly.d_isz_h); cudaFree(ly.d_m); cudaFree(ly.d_fac); cudaFree(ly.d_dinv);
-    }
-    cudaFree(c.d_coefs);
-    cudaFree(c.d_sx_n); cudaFree(c.d_isx_h); cudaFree(c.d_sy_n); cudaFree(c.d_isy_h);
-    cudaFree(c.d_sz_n); cudaFree(c.d_isz_h); cudaFree(c.d_m); cudaFree(c.d_flag);
     delete h;
     return HZ_OK;
+}
+
+hz_status hz_create_shared(hz_handle* src, void* stream, hz_handle** out) {
+    if (out) *out = nullptr;
+    if (!src || !out) return HZ_ERR_ARG;
+    if (!src->ctx.factored) {
+        src->ctx.last_error = "hz_create_shared: the source handle is not factored";
+        return HZ_ERR_STATE;
+    }
+    hz_handle* h = nullptr;
+    try {
+        h = new hz_handle();
+        Ctx& c = h->ctx;
+        const Ctx& s = src->ctx;
+        c.nx = s.nx; c.ny = s.ny; c.nz = s.nz; c.h = s.h; c.omega = s.omega; c.C = s.C;
+        c.npml = s.npml; c.npml_loc = s.npml_loc; c.L = s.L; c.K = s.K; c.prec = s.prec;
+        c.P = s.P; c.ntr = s.ntr; c.device = s.device;
+        c.shapes = s.shapes;    // host copies; device arrays borrowed
+        c.layers = s.layers;    // factors borrowed
+        c.d_coefs = s.d_coefs;
+        c.d_sx_n = s.d_sx_n; c.d_isx_h = s.d_isx_h; c.d_sy_n = s.d_sy_n; c.d_isy_h = s.d_isy_h;
+        c.d_sz_n = s.d_sz_n; c.d_isz_h = s.d_isz_h; c.d_m = s.d_m;
+        c.use_tc = s.use_tc; c.tc_ks = s.tc_ks; c.tc_min_tiles = s.tc_min_tiles;
+        c.autotune = s.autotune; c.use_graphs = s.use_graphs;
+        c.tuned = s.tuned;
+        c.factored = true;
+        c.owns_shared = false;
+        c.stream = (cudaStream_t)stream;
+        c.d_flag = (int*)dev_alloc(4 * sizeof(int));
+        HZ_CUDA(cudaMemset(c.d_flag, 0, 4 * sizeof(int)));
+        HZ_CUDA(cudaDeviceSynchronize());
+        *out = h;
+        return HZ_OK;
+    } catch (const Error& e) {
+        if (h) { h->ctx.owns_shared = false; hz_destroy(h); }
+        src->ctx.last_error = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc&) {
+        if (h) { h->ctx.owns_shared = false; hz_destroy(h); }
+        return HZ_ERR_OOM;
+    }
 }
 
 const char* hz_last_error(const hz_handle* h) {

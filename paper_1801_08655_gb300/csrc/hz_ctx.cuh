@@ -144,6 +144,7 @@ struct Ctx {
     double* d_m = nullptr;
     int* d_flag = nullptr;   // device error flags: [0] tiny pivot
     bool factored = false;
+    bool owns_shared = true;  // false for handles that borrow another handle's factors (hz_create_shared)
     long long workspace_bytes = 0;
     float factor_ms = 0.f;
     // solve workspaces

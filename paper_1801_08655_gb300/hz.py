@@ -28,7 +28,7 @@ EXPORTED = [
     "hz_layer_info", "hz_factor_stats", "hz_layer_solve_cost", "hz_layer_solve", "hz_polarized_rhs",
     "hz_apply_mpol", "hz_apply_precond", "hz_reconstruct", "hz_volume_residual",
     "hz_profile_begin", "hz_profile_end", "hz_kernel_launches", "hz_volume_residual_noalloc",
-    "hz_tuning_report", "hz_solve_group",
+    "hz_tuning_report", "hz_solve_group", "hz_create_shared",
 ]
 
 
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.hz_profile_end.argtypes = [VP, P(ct.c_int64), P(D), P(D), P(D)]
     lib.hz_kernel_launches.argtypes = []
     lib.hz_tuning_report.argtypes = [VP]
+    lib.hz_create_shared.argtypes = [VP, VP, P(VP)]
     lib.hz_solve_group.argtypes = [P(VP), I32, P(VP), P(I32), P(VP), P(SolveOpts), P(VP), P(ct.c_int)]
     for name in EXPORTED:
         if name not in ("hz_default_opts", "hz_last_error", "hz_kernel_launches", "hz_tuning_report"):
@@ -134,6 +135,22 @@ class Solver:
         if st != HZ_OK:
             raise HzError(st, self.lib.hz_last_error(None).decode())
         self.h = hnd
+
+    @classmethod
+    def shared(cls, src: "Solver", stream=None) -> "Solver":
+        """A second handle on src's resident factors with its own workspaces and stream."""
+        import torch
+        obj = cls.__new__(cls)
+        obj.lib = src.lib
+        obj.shape, obj.precision, obj.n_layers, obj.K, obj.P = src.shape, src.precision, src.n_layers, src.K, src.P
+        obj.stream = stream if stream is not None else torch.cuda.Stream()
+        hnd = ct.c_void_p()
+        st = obj.lib.hz_create_shared(src.h, ct.c_void_p(obj.stream.cuda_stream), ct.byref(hnd))
+        if st != HZ_OK:
+            raise HzError(st, obj.lib.hz_last_error(src.h).decode())
+        obj.h = hnd
+        obj._src = src  # keep the factor owner alive
+        return obj
 
     # -------------------------------------------------------------------- plumbing
     def _check(self, st: int, allow=(HZ_OK,)):
