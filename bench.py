@@ -96,13 +96,6 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
-
-
 def cpu_oracle_sample(reps: int = 1):
     """Time the oracle (global FP64 sparse direct solve) on the bounded sample."""
     from oracle import direct
@@ -130,7 +123,8 @@ def sample_text():
 
 
 def run_reference(args):
-    ws, rank, local = dist_setup()
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     for _ in range(args.warmup):
@@ -158,7 +152,8 @@ def run_ours(args):
     import torch
     from paper_1801_08655_gb300 import build, hz, workloads as W
 
-    ws, rank, local = dist_setup()
+    from paper_1801_08655_gb300 import replicas
+    ws, rank, local = replicas.env_ranks()
     if ws > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -199,8 +194,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         _, infos, _ = s.solve(rhs, opts, u=u)
     # ---------------- timed region
-    if ws > 1:
-        torch.distributed.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
@@ -218,16 +212,11 @@ def run_ours(args):
     tuning = [ln for ln in s.tuning_report().splitlines() if ln]
     launches = hz.kernel_launches() - launches0
     torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
+    replicas.barrier()
     clk = clocks.stop()
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * R * args.steps / (total_ms / 1e3)
+    value = replicas.whole_job_rate(R * args.steps, sum(step_ms) / 1e3)
+    total_ms = 1e3 * replicas.max_over_ranks(sum(step_ms) / 1e3)
     vol_res = max(i.volume_relres for i in step_infos[-1])
     iters = step_infos[-1][0].iters
     refin = step_infos[-1][0].refinements
@@ -240,18 +229,14 @@ def run_ours(args):
         u_h = torch.empty_like(rhs_h).pin_memory()
         rn, un = rhs_h.numpy(), u_h.numpy()
         s.solve_host(rn, opts, u=un)  # warm the staging path
-        if ws > 1:
-            torch.distributed.barrier()
+        replicas.barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             s.solve_host(rn, opts, u=un)
         e2e_s = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
         nbytes = R * N3 * 16
-        e2e = {"value": ws * R * args.e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        e2e = {"value": replicas.whole_job_rate(R * args.e2e_steps, e2e_s), "unit": UNIT,
+               "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes}
         del rhs_h, u_h
 

@@ -54,8 +54,11 @@ typedef enum {
 
 typedef enum {
     HZ_PREC_FP64 = 0,  /* complex128 factors and local solves, FP64 GMRES */
-    HZ_PREC_MIXED = 1  /* complex64 factors and local solves (FP64 pivot blocks), FP64 GMRES
+    HZ_PREC_MIXED = 1, /* complex64 factors and local solves (FP64 pivot blocks), FP64 GMRES
                           on the traces, FP64 volume residual + defect correction */
+    HZ_PREC_MIXED_FP64_FACTOR = 2  /* as HZ_PREC_MIXED online, but the offline factorization runs in
+                          FP64 and its factors are rounded to complex64 (slower factorization,
+                          more accurate local solves) */
 } hz_precision;
 
 typedef struct { int32_t nx, ny, nz; double h; } hz_grid;

@@ -86,6 +86,52 @@ void d2h(Ctx& c, void* dst, const void* src, size_t bytes) {
 
 size_t elem_size(const Ctx& c) { return c.prec == HZ_PREC_FP64 ? sizeof(double2) : sizeof(float2); }
 
+__global__ void k_demote(float2* dst, const double2* src, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = make_float2((float)src[i].x, (float)src[i].y);
+}
+
+// FP64 factorization into temporary complex128 storage, then rounding to the complex64 factors.
+void factor_fp64_demote(Ctx& c) {
+    std::vector<void*> tmp_fac, tmp_dinv;
+    try {
+        for (auto& ly : c.layers) {
+            const Shape& sh = c.shapes[ly.shape];
+            tmp_fac.push_back(dev_alloc((size_t)sh.factor_tiles * TILE2 * sizeof(double2)));
+            tmp_dinv.push_back(dev_alloc((size_t)sh.N * sizeof(double2)));
+        }
+        std::vector<std::pair<void*, void*>> keep;
+        for (size_t l = 0; l < c.layers.size(); ++l) {
+            keep.push_back({c.layers[l].d_fac, c.layers[l].d_dinv});
+            c.layers[l].d_fac = tmp_fac[l];
+            c.layers[l].d_dinv = tmp_dinv[l];
+        }
+        try {
+            factor_layers<double2>(c);
+        } catch (...) {
+            for (size_t l = 0; l < c.layers.size(); ++l) { c.layers[l].d_fac = keep[l].first; c.layers[l].d_dinv = keep[l].second; }
+            throw;
+        }
+        for (size_t l = 0; l < c.layers.size(); ++l) {
+            c.layers[l].d_fac = keep[l].first;
+            c.layers[l].d_dinv = keep[l].second;
+            const Shape& sh = c.shapes[c.layers[l].shape];
+            k_demote<<<4096, 256, 0, c.stream>>>((float2*)c.layers[l].d_fac, (const double2*)tmp_fac[l],
+                                                 sh.factor_tiles * TILE2);
+            HZ_CHECK_LAUNCH();
+            k_demote<<<1024, 256, 0, c.stream>>>((float2*)c.layers[l].d_dinv, (const double2*)tmp_dinv[l], sh.N);
+            HZ_CHECK_LAUNCH();
+        }
+        HZ_CUDA(cudaStreamSynchronize(c.stream));
+    } catch (...) {
+        for (void* p : tmp_fac) cudaFree(p);
+        for (void* p : tmp_dinv) cudaFree(p);
+        throw;
+    }
+    for (void* p : tmp_fac) cudaFree(p);
+    for (void* p : tmp_dinv) cudaFree(p);
+}
+
 void release_slots(Ctx& c) {
     c.plans.clear();  // recorded plans point into the slot batches
     free_batches(c);
@@ -178,10 +224,10 @@ void do_solve(Ctx& c, const double2* rhs, int R, double2* u, const hz_solve_opts
                     if (worst <= o.refine_tol || passes >= o.max_refine) break;
                     // defect correction: A du = r with the mixed path, u += du.  The correction
                     // only needs the digits that bring the residual below refine_tol, so its GMRES
-                    // tolerance is relaxed accordingly (never looser than 1e-3).
+                    // tolerance is relaxed accordingly (never looser than 1e-1).
                     std::vector<hz_solve_info> inf2(R);
                     hz_solve_opts o2 = o;
-                    o2.gmres_tol = std::max(o.gmres_tol, std::min(1e-3, 0.1 * o.refine_tol / std::max(worst, 1e-300)));
+                    o2.gmres_tol = std::max(o.gmres_tol, std::min(1e-1, 0.1 * o.refine_tol / std::max(worst, 1e-300)));
                     gmres_solve<float2>(c, res, false, R, du, o2, inf2.data());
                     k_axpy_vol<<<cdiv((long long)R * N3, 256), 256, 0, c.stream>>>(u, du, (long long)R * N3);
                     HZ_CHECK_LAUNCH();
@@ -248,7 +294,7 @@ extern "C" {
 
 void hz_default_opts(hz_precision prec, hz_solve_opts* o) {
     if (!o) return;
-    o->gmres_tol = prec == HZ_PREC_FP64 ? 1e-10 : 1e-7;
+    o->gmres_tol = prec == HZ_PREC_FP64 ? 1e-10 : 1e-7;  // mixed modes: 1e-7
     o->restart = 12;
     o->max_iter = 100;
     o->refine_tol = 1e-9;
@@ -264,7 +310,8 @@ hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz
         if (grid->nx < 3 || grid->ny < 3 || grid->nz < 3 || !(grid->h > 0)) throw Error{HZ_ERR_ARG, "grid"};
         if (!(omega > 0) || !std::isfinite(omega)) throw Error{HZ_ERR_ARG, "omega must be > 0"};
         if (pml->npml < 0 || !(pml->C >= 0)) throw Error{HZ_ERR_ARG, "pml"};
-        if (prec != HZ_PREC_FP64 && prec != HZ_PREC_MIXED) throw Error{HZ_ERR_ARG, "precision"};
+        if (prec != HZ_PREC_FP64 && prec != HZ_PREC_MIXED && prec != HZ_PREC_MIXED_FP64_FACTOR)
+            throw Error{HZ_ERR_ARG, "precision"};
         const int nz = grid->nz;
         const int nphys = nz - 2 * pml->npml;
         if (n_layers < 1 || nphys < n_layers) throw Error{HZ_ERR_ARG, "n_layers out of range"};
@@ -401,6 +448,7 @@ hz_status hz_factor(hz_handle* h) {
         HZ_CUDA(cudaEventCreate(&e1));
         HZ_CUDA(cudaEventRecord(e0, c.stream));
         if (c.prec == HZ_PREC_FP64) factor_layers<double2>(c);
+        else if (c.prec == HZ_PREC_MIXED_FP64_FACTOR) factor_fp64_demote(c);
         else factor_layers<float2>(c);
         HZ_CUDA(cudaEventRecord(e1, c.stream));
         HZ_CUDA(cudaEventSynchronize(e1));

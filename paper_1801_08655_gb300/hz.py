@@ -21,7 +21,7 @@ HZ_OK, HZ_ERR_ARG, HZ_ERR_OOM, HZ_ERR_ADMISSION, HZ_ERR_STATE, HZ_ERR_NONFINITE,
     HZ_ERR_NO_CONVERGENCE, HZ_ERR_TIMEOUT, HZ_ERR_CUDA = range(10)
 STATUS_NAMES = ["HZ_OK", "HZ_ERR_ARG", "HZ_ERR_OOM", "HZ_ERR_ADMISSION", "HZ_ERR_STATE", "HZ_ERR_NONFINITE",
                 "HZ_ERR_PIVOT", "HZ_ERR_NO_CONVERGENCE", "HZ_ERR_TIMEOUT", "HZ_ERR_CUDA"]
-PREC = {"fp64": 0, "mixed": 1}
+PREC = {"fp64": 0, "mixed": 1, "mixed64": 2}
 
 EXPORTED = [
     "hz_default_opts", "hz_create", "hz_factor", "hz_solve", "hz_solve_host", "hz_destroy", "hz_last_error",

@@ -84,7 +84,7 @@ class Server:
         nz, ny, nx = self.shape
         s = self.primaries[0]
         L, K = s.n_layers, s.K
-        esz = 8 if s.precision == "mixed" else 16
+        esz = 16 if s.precision == "fp64" else 8
         lay = 0
         for ell in range(L):
             lo, hi, zlo, zhi = s.layer_info(ell)
