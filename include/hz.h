@@ -226,6 +226,12 @@ hz_status hz_volume_residual(hz_handle* h, const double* rhs, const double* u, i
  * hz_profile_end synchronizes the handle's stream and returns the number of recorded
  * substitution calls, their summed device time in ms, and the summed algorithmic factor
  * bytes (each stored factor entry read once forward and once backward) and real flops.
+ * hz_profile_begin_detail does the same and also records events around every kernel launch
+ * of those substitutions; hz_profile_kernel then returns, per kernel kind, the launches, their
+ * summed device time in ms and their algorithmic factor bytes and real flops over the interval
+ * closed by the last hz_profile_end (kind 0: CUDA-core substitution kernels, 1: tensor-core
+ * kernel; any other kind is HZ_ERR_ARG).  Detail mode adds an event pair per launch and
+ * replaces CUDA-graph replay by direct launches: profile an interval apart from timed runs.
  * hz_kernel_launches returns the number of kernels the library has launched in this
  * process (all handles).
  * ------------------------------------------------------------------------------------ */
@@ -250,7 +256,10 @@ hz_status hz_volume_residual_noalloc(hz_handle* h, const double* rhs, const doub
                                      double* relres_host);
 
 hz_status hz_profile_begin(hz_handle* h);
+hz_status hz_profile_begin_detail(hz_handle* h);
 hz_status hz_profile_end(hz_handle* h, int64_t* calls, double* total_ms, double* alg_bytes, double* alg_flops);
+hz_status hz_profile_kernel(hz_handle* h, int32_t kind, int64_t* launches, double* total_ms, double* alg_bytes,
+                            double* alg_flops);
 int64_t hz_kernel_launches(void);
 
 /* The substitution autotuner's record for this handle: one line per tuned batch signature

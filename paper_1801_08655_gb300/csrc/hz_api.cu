@@ -411,7 +411,7 @@ hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz
         }
         c.d_coefs = dev_copy(coefs);
         HZ_CUDA(cudaGetDevice(&c.device));
-        if (const char* e = std::getenv("HZ_SUBST_TC")) c.use_tc = std::atoi(e) != 0;
+        if (const char* e = std::getenv("HZ_SUBST_TC")) c.tc_mode = std::max(0, std::min(2, std::atoi(e)));
         if (const char* e = std::getenv("HZ_TC_KS")) c.tc_ks = std::max(1, std::atoi(e));
         if (const char* e = std::getenv("HZ_AUTOTUNE")) c.autotune = std::atoi(e) != 0;
         if (const char* e = std::getenv("HZ_GRAPHS")) c.use_graphs = std::atoi(e) != 0;
@@ -549,7 +549,7 @@ hz_status hz_create_shared(hz_handle* src, void* stream, hz_handle** out) {
         c.d_coefs = s.d_coefs;
         c.d_sx_n = s.d_sx_n; c.d_isx_h = s.d_isx_h; c.d_sy_n = s.d_sy_n; c.d_isy_h = s.d_isy_h;
         c.d_sz_n = s.d_sz_n; c.d_isz_h = s.d_isz_h; c.d_m = s.d_m;
-        c.use_tc = s.use_tc; c.tc_ks = s.tc_ks; c.tc_min_tiles = s.tc_min_tiles;
+        c.tc_mode = s.tc_mode; c.tc_ks = s.tc_ks; c.tc_min_tiles = s.tc_min_tiles;
         c.autotune = s.autotune; c.use_graphs = s.use_graphs;
         c.tuned = s.tuned;
         c.factored = true;
@@ -718,20 +718,29 @@ hz_status hz_volume_residual(hz_handle* h, const double* rhs, const double* u, i
     })
 }
 
-hz_status hz_profile_begin(hz_handle* h) {
+static hz_status profile_begin(hz_handle* h, bool detail) {
     if (!h) return HZ_ERR_ARG;
     Ctx& c = h->ctx;
-    for (auto& r : c.prof_recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
-    c.prof_recs.clear();
+    for (auto* v : {&c.prof_recs, &c.prof_launch}) {
+        for (auto& r : *v) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+        v->clear();
+    }
+    c.kern_stat[0] = KernStat{};
+    c.kern_stat[1] = KernStat{};
     c.prof = true;
+    c.prof_detail = detail;
     return HZ_OK;
 }
+
+hz_status hz_profile_begin(hz_handle* h) { return profile_begin(h, false); }
+hz_status hz_profile_begin_detail(hz_handle* h) { return profile_begin(h, true); }
 
 hz_status hz_profile_end(hz_handle* h, int64_t* calls, double* total_ms, double* alg_bytes, double* alg_flops) {
     if (!h) return HZ_ERR_ARG;
     HZ_TRY(h, {
         Ctx& c = h->ctx;
         c.prof = false;
+        c.prof_detail = false;
         HZ_CUDA(cudaStreamSynchronize(c.stream));
         double ms = 0, by = 0, fl = 0;
         for (auto& r : c.prof_recs) {
@@ -743,13 +752,40 @@ hz_status hz_profile_end(hz_handle* h, int64_t* calls, double* total_ms, double*
             cudaEventDestroy(r.e0);
             cudaEventDestroy(r.e1);
         }
+        for (auto& r : c.prof_launch) {
+            float t = 0.f;
+            HZ_CUDA(cudaEventElapsedTime(&t, r.e0, r.e1));
+            KernStat& k = c.kern_stat[r.kind];
+            k.launches += 1;
+            k.ms += t;
+            k.bytes += r.bytes;
+            k.flops += r.flops;
+            cudaEventDestroy(r.e0);
+            cudaEventDestroy(r.e1);
+        }
         if (calls) *calls = (int64_t)c.prof_recs.size();
         c.prof_recs.clear();
+        c.prof_launch.clear();
         if (total_ms) *total_ms = ms;
         if (alg_bytes) *alg_bytes = by;
         if (alg_flops) *alg_flops = fl;
         return HZ_OK;
     })
+}
+
+hz_status hz_profile_kernel(hz_handle* h, int32_t kind, int64_t* launches, double* total_ms, double* alg_bytes,
+                            double* alg_flops) {
+    if (!h) return HZ_ERR_ARG;
+    if (kind < 0 || kind > 1) {
+        h->ctx.last_error = "hz_profile_kernel: kind must be 0 (CUDA-core) or 1 (tensor-core)";
+        return HZ_ERR_ARG;
+    }
+    const KernStat& k = h->ctx.kern_stat[kind];
+    if (launches) *launches = k.launches;
+    if (total_ms) *total_ms = k.ms;
+    if (alg_bytes) *alg_bytes = k.bytes;
+    if (alg_flops) *alg_flops = k.flops;
+    return HZ_OK;
 }
 
 int64_t hz_kernel_launches(void) { return (int64_t)hz::g_launch_count.load(); }

@@ -42,10 +42,15 @@ struct Batch {
     std::vector<long long> vec_rows;
     double alg_bytes = 0;       // factor bytes one forward+backward substitution streams (all jobs)
     double flops_per_col = 0;   // real flops per right-hand-side column (all jobs)
+    // algorithmic factor bytes and real flops per column of each launch, by kernel kind
+    // (0 CUDA-core, 1 tensor-core), phase and level
+    std::vector<double> lvl_bytes[2][4], lvl_flops[2][4];
 };
 
-// Event-timed record of substitution calls (enabled by hz_profile_begin).
-struct ProfRec { cudaEvent_t e0, e1; double bytes, flops; };
+// Event-timed record of a substitution call (hz_profile_begin) or, in detail mode, of one
+// kernel launch of it (kind 0 CUDA-core, 1 tensor-core).
+struct ProfRec { cudaEvent_t e0, e1; double bytes, flops; int kind; };
+struct KernStat { long long launches = 0; double ms = 0, bytes = 0, flops = 0; };
 
 // Recorded sequence of stream operations with the device descriptors it owns.  run() issues
 // the operations on a stream; run_graph() captures them once into a CUDA graph and replays it.
@@ -55,6 +60,7 @@ struct Rec {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t upload_stream = 0;
+    long long graph_kernels = 0;   // kernels in the captured graph (counted again at every replay)
     Rec() = default;
     Rec(const Rec&) = delete;
     Rec& operator=(const Rec&) = delete;
@@ -89,6 +95,7 @@ struct Rec {
                 cudaStreamDestroy(cs);
                 throw Error{HZ_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e)};
             }
+            const long long k0 = g_launch_count.load();
             try {
                 run(cs);
             } catch (...) {
@@ -103,6 +110,10 @@ struct Rec {
             cudaStreamDestroy(cs);
             if (e != cudaSuccess) throw Error{HZ_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e)};
             HZ_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+            // the capture counted the kernels once (as launched by this first replay)
+            graph_kernels = g_launch_count.load() - k0;
+        } else {
+            g_launch_count.fetch_add(graph_kernels, std::memory_order_relaxed);
         }
         HZ_CUDA(cudaGraphLaunch(exec, st));
     }
@@ -158,12 +169,17 @@ struct Ctx {
     std::map<long long, std::unique_ptr<Rec>> plans;   // matvec plans by column count
     // autotuner: (shape signature, ldc) -> chosen split-K depth and column chunk
     bool autotune = true;
-    std::map<std::string, std::pair<int, int>> tuned;
+    struct TuneChoice { int KS, CC, tc, KS_tc; };
+    std::map<std::string, TuneChoice> tuned;
     std::vector<std::string> tune_log;
-    bool use_tc = false;    // tensor-core substitution for complex64 at >= 64 columns (opt-in)
+    int tc_mode = 2;        // tensor-core substitution (complex64, >= 64 columns): 0 never, 1 always,
+                            // 2 when the autotuner measures it faster for the batch signature
     int tc_ks = 4;          // split-K (factor tiles per block) of small tensor-core batches
-    int tc_min_tiles = 3;   // output tiles a node product needs to run on the tensor cores
+    int tc_min_tiles = 8;   // output tiles a node product needs to run on the tensor cores
     std::vector<ProfRec> prof_recs;
+    bool prof_detail = false;                 // also time every substitution launch by kernel kind
+    std::vector<ProfRec> prof_launch;
+    KernStat kern_stat[2];                    // per kind, from the last hz_profile_end
 };
 
 template <class C> void factor_layers(Ctx& ctx);

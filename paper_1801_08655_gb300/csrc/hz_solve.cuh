@@ -14,7 +14,8 @@ int padded_ldc(bool is_double, int ncols);
 // Job set with per-level task lists, cached by layer list.
 template <class C> Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols);
 // Build (or fetch) a batch with an explicit split-K depth and column chunk.
-template <class C> Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS, int CC);
+template <class C> Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS, int CC, bool tc,
+                                       int KS_tc);
 // Autotune the substitution of this batch signature (times candidate split-K depths and column
 // chunks on zeroed slot vectors); a no-op once the signature is tuned or when tuning is off.
 template <class C> void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols);

@@ -36,6 +36,63 @@ template <> __device__ inline void atomic_sub<double2>(double2* p, double2 v) {
 }
 template <class C> __device__ inline void atomic_add(C* p, C v) { atomic_sub(p, cneg(v)); }
 
+// Writes the TILE x CC output block of one task, staged in shared memory (Ys, row pitch YP),
+// to the solve vectors: consecutive threads take consecutive columns of a row, and every thread
+// issues all of its loads (row indices, D^{-1}, z) before any of its writes.  A task covering
+// the whole reduction of its rows is their only writer and stores; split reductions and FB
+// (update rows are shared between the nodes of a level) accumulate atomically.  Outputs are
+// zeroed beforehand (x before the forward pass and, for BB, by BA; acc before the backward).
+template <class C, int CC, int MODE>
+__device__ inline void write_out(const C* Ys, int YP, const JobDev<C>& jb, const NodeDev& nd, const int* upd,
+                                 int tile, int col0, int ldc, int kt0, bool unique) {
+    constexpr int EPT = (TILE * CC + 255) / 256;   // elements per thread
+    constexpr int EB = EPT < 4 ? EPT : 4;          // elements per load batch
+    const int nrows = (MODE == FB) ? nd.nupd : nd.nown;
+#pragma unroll
+    for (int i0 = 0; i0 < EPT; i0 += EB) {
+        long long dst[EB];
+        C y[EB], z[EB], di[EB];
+        bool v[EB];
+#pragma unroll
+        for (int i = 0; i < EB; ++i) {
+            const int e = threadIdx.x + 256 * (i0 + i);
+            const int r = e / CC, c = e % CC;
+            const int row = tile * TILE + r;
+            v[i] = e < TILE * CC && row < nrows;
+            dst[i] = 0;
+            y[i] = czero<C>();
+            z[i] = czero<C>();
+            di[i] = czero<C>();
+            if (v[i]) {
+                dst[i] = ((MODE == FB) ? (long long)upd[row] : (long long)(nd.own0 + row)) * ldc + col0 + c;
+                y[i] = Ys[r * YP + c];
+                if (MODE == BA && kt0 == 0) {
+                    di[i] = jb.dinv[nd.own0 + row];
+                    z[i] = jb.x[dst[i]];
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < EB; ++i) {
+            if (!v[i]) continue;
+            if (MODE == FB) {
+                atomic_sub(jb.acc + dst[i], y[i]);
+            } else if (MODE == FA || MODE == BB) {
+                if (unique) jb.x[dst[i]] = y[i];
+                else atomic_add(jb.x + dst[i], y[i]);
+            } else {  // BA: acc = Dinv z - L21^T x_upd; the task with the first reduction tile clears z
+                C val = y[i];
+                if (kt0 == 0) {
+                    val = csub(val, cmul(di[i], z[i]));
+                    jb.x[dst[i]] = czero<C>();
+                }
+                if (unique) jb.acc[dst[i]] = cneg(val);
+                else atomic_sub(jb.acc + dst[i], val);
+            }
+        }
+    }
+}
+
 template <class C, int CC, int MODE>
 __global__ void __launch_bounds__(256) k_subst(const Task* __restrict__ tasks,
                                                const JobDev<C>* __restrict__ jobs, int ldc, int nchunks,
@@ -125,45 +182,27 @@ __global__ void __launch_bounds__(256) k_subst(const Task* __restrict__ tasks,
         __syncthreads();
     }
 
+    // stage the TILE x CC outputs in Ms (free after the loop), then write them row-wise
     if (WK > 1) {
 #pragma unroll
         for (int u = 0; u < NCT; ++u) Red[wk][lane * CC + wc * NCT + u] = acc[u];
         __syncthreads();
-        if (wk != 0) return;
-#pragma unroll
-        for (int u = 0; u < NCT; ++u) {
-            C s = czero<C>();
-            for (int q = 0; q < WK; ++q) s = cadd(s, Red[q][lane * CC + wc * NCT + u]);
-            acc[u] = s;
-        }
-    }
-
-    const int row = tk.tile * TILE + lane;
-    if (MODE == FB) {
-        if (row >= nd.nupd) return;
-        C* dst = jb.acc + (long long)upd[row] * ldc + col0 + wc * NCT;
-#pragma unroll
-        for (int u = 0; u < NCT; ++u) atomic_sub(dst + u, acc[u]);
-        return;
-    }
-    if (row >= nd.nown) return;
-    const long long e = (long long)(nd.own0 + row) * ldc + col0 + wc * NCT;
-    if (MODE == FA || MODE == BB) {  // outputs zeroed beforehand (x before the forward, by BA after)
-#pragma unroll
-        for (int u = 0; u < NCT; ++u) atomic_add(jb.x + e + u, acc[u]);
-    } else {  // BA: v = Dinv z - L21^T x_upd accumulated in acc (zeroed before the backward)
-        if (kt0 == 0) {
-            // the only task that reads z of these rows; it clears them for BB's accumulation
-            const C di = jb.dinv[nd.own0 + row];
+        if (wk == 0) {
 #pragma unroll
             for (int u = 0; u < NCT; ++u) {
-                acc[u] = csub(acc[u], cmul(di, jb.x[e + u]));
-                jb.x[e + u] = czero<C>();
+                C s = czero<C>();
+                for (int q = 0; q < WK; ++q) s = cadd(s, Red[q][lane * CC + wc * NCT + u]);
+                acc[u] = s;
             }
         }
-#pragma unroll
-        for (int u = 0; u < NCT; ++u) atomic_sub(jb.acc + e + u, acc[u]);
     }
+    if (wk == 0) {
+#pragma unroll
+        for (int u = 0; u < NCT; ++u) Ms[lane][wc * NCT + u] = acc[u];
+    }
+    __syncthreads();
+    const bool unique = kt0 == ((MODE == BB) ? tk.tile : 0) && kt1 == kend;
+    write_out<C, CC, MODE>(&Ms[0][0], TILE + 1, jb, nd, upd, tk.tile, col0, ldc, kt0, unique);
 }
 
 // 64-column variant for complex64: each thread owns a 2-row x 4-column register tile, fed by
@@ -176,8 +215,9 @@ __global__ void __launch_bounds__(256, 4) k_subst64(const Task* __restrict__ tas
                                                     int KS) {
     constexpr int CC = 64;
     constexpr int MS = 34;                       // padded row length (complex) of the [k][row] tile
+    constexpr int XP = CC + 2;                   // padded row length of the vector / output tile
     __shared__ __align__(16) float2 Ms[TILE][MS];
-    __shared__ __align__(16) float2 Xs[TILE][CC];
+    __shared__ __align__(16) float2 Xs[TILE][XP];
 
     const int chunk = blockIdx.x % nchunks;
     const Task tk = tasks[blockIdx.x / nchunks];
@@ -260,35 +300,15 @@ __global__ void __launch_bounds__(256, 4) k_subst64(const Task* __restrict__ tas
         __syncthreads();
     }
 
+    // stage the 32 x 64 outputs in Xs (free after the loop), then write them row-wise
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-        const int row = tk.tile * TILE + 2 * rp + i;
-        const int col = col0 + 4 * cq;
-        if (MODE == FB) {
-            if (row >= nd.nupd) continue;
-            float2* dst = jb.acc + (long long)upd[row] * ldc + col;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) atomic_sub(dst + j, acc[i][j]);
-            continue;
-        }
-        if (row >= nd.nown) continue;
-        const long long e = (long long)(nd.own0 + row) * ldc + col;
-        if (MODE == FA || MODE == BB) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) atomic_add(jb.x + e + j, acc[i][j]);
-        } else {
-            if (kt0 == 0) {
-                const float2 di = jb.dinv[nd.own0 + row];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    acc[i][j] = csub(acc[i][j], cmul(di, jb.x[e + j]));
-                    jb.x[e + j] = make_float2(0.f, 0.f);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) atomic_sub(jb.acc + e + j, acc[i][j]);
-        }
+        *(float4*)&Xs[2 * rp + i][4 * cq] = make_float4(acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y);
+        *(float4*)&Xs[2 * rp + i][4 * cq + 2] = make_float4(acc[i][2].x, acc[i][2].y, acc[i][3].x, acc[i][3].y);
     }
+    __syncthreads();
+    const bool unique = kt0 == ((MODE == BB) ? tk.tile : 0) && kt1 == kend;
+    write_out<float2, CC, MODE>(&Xs[0][0], XP, jb, nd, upd, tk.tile, col0, ldc, kt0, unique);
 }
 
 template <class C, int CC>
@@ -326,22 +346,47 @@ void zero_vectors(const Batch& b, bool x_vec, int ldc, cudaStream_t st) {
     }
 }
 
+// Records a CUDA event pair around one launch in profiling detail mode.
+struct LaunchTimer {
+    std::vector<ProfRec>* out;
+    cudaStream_t st;
+    ProfRec r{};
+    LaunchTimer(std::vector<ProfRec>* o, cudaStream_t s, int kind, double bytes, double flops) : out(o), st(s) {
+        if (!out) return;
+        r.kind = kind;
+        r.bytes = bytes;
+        r.flops = flops;
+        HZ_CUDA(cudaEventCreate(&r.e0));
+        HZ_CUDA(cudaEventCreate(&r.e1));
+        HZ_CUDA(cudaEventRecord(r.e0, st));
+    }
+    void done() {
+        if (!out) return;
+        HZ_CUDA(cudaEventRecord(r.e1, st));
+        out->push_back(r);
+    }
+};
+
 template <class C, int CC>
-void run_batch(const Batch& b, int ldc, bool tc, int* flag, cudaStream_t st) {
+void run_batch(const Batch& b, int ldc, int ncols, bool tc, int* flag, cudaStream_t st, std::vector<ProfRec>* pl) {
+    auto level = [&](int h, int mode) {
+        if (b.cnt[mode][h] > 0) {
+            LaunchTimer lt(pl, st, 0, b.lvl_bytes[0][mode][h], b.lvl_flops[0][mode][h] * ncols);
+            launch_level<C, CC>(b, h, mode, ldc, st);
+            lt.done();
+        }
+        if (tc && b.pair_cnt[mode][h] > 0) {
+            LaunchTimer lt(pl, st, 1, b.lvl_bytes[1][mode][h], b.lvl_flops[1][mode][h] * ncols);
+            launch_level_tc(b, h, mode, ldc, flag, st);
+            lt.done();
+        }
+    };
     zero_vectors<C>(b, true, ldc, st);
-    for (int h = 0; h < b.H; ++h) {
-        for (int mode : {FA, FB}) {
-            launch_level<C, CC>(b, h, mode, ldc, st);
-            if (tc) launch_level_tc(b, h, mode, ldc, flag, st);
-        }
-    }
+    for (int h = 0; h < b.H; ++h)
+        for (int mode : {FA, FB}) level(h, mode);
     zero_vectors<C>(b, false, ldc, st);
-    for (int h = b.H - 1; h >= 0; --h) {
-        for (int mode : {BA, BB}) {
-            launch_level<C, CC>(b, h, mode, ldc, st);
-            if (tc) launch_level_tc(b, h, mode, ldc, flag, st);
-        }
-    }
+    for (int h = b.H - 1; h >= 0; --h)
+        for (int mode : {BA, BB}) level(h, mode);
 }
 
 }  // namespace
@@ -371,15 +416,16 @@ void substitute(Ctx& ctx, const Batch& b, int ncols, cudaStream_t st) {
     }
     const bool tc = b.tc;
     int* flag = ctx.d_flag + 1;
+    std::vector<ProfRec>* pl = (ctx.prof && ctx.prof_detail) ? &ctx.prof_launch : nullptr;
     switch (cc) {
-        case 1: run_batch<C, 1>(b, ldc, tc, flag, st); break;
-        case 2: run_batch<C, 2>(b, ldc, tc, flag, st); break;
-        case 4: run_batch<C, 4>(b, ldc, tc, flag, st); break;
-        case 8: run_batch<C, 8>(b, ldc, tc, flag, st); break;
-        case 16: run_batch<C, 16>(b, ldc, tc, flag, st); break;
-        case 32: run_batch<C, 32>(b, ldc, tc, flag, st); break;
+        case 1: run_batch<C, 1>(b, ldc, ncols, tc, flag, st, pl); break;
+        case 2: run_batch<C, 2>(b, ldc, ncols, tc, flag, st, pl); break;
+        case 4: run_batch<C, 4>(b, ldc, ncols, tc, flag, st, pl); break;
+        case 8: run_batch<C, 8>(b, ldc, ncols, tc, flag, st, pl); break;
+        case 16: run_batch<C, 16>(b, ldc, ncols, tc, flag, st, pl); break;
+        case 32: run_batch<C, 32>(b, ldc, ncols, tc, flag, st, pl); break;
         default:
-            if constexpr (sizeof(C) == 8) run_batch<C, 64>(b, ldc, tc, flag, st);
+            if constexpr (sizeof(C) == 8) run_batch<C, 64>(b, ldc, ncols, tc, flag, st, pl);
             else throw Error{HZ_ERR_ARG, "chunk width"};
     }
     if (ctx.prof) {
@@ -398,11 +444,11 @@ static bool tc_node(int mode, const Node& nd, int min_tiles) {
     return out_t >= min_tiles && red_t >= 2;
 }
 
-static std::string tune_key(const Ctx& ctx, const std::vector<int>& layers, int ldc, bool tc) {
+static std::string tune_key(const Ctx& ctx, const std::vector<int>& layers, int ldc) {
     std::vector<int> shapes;
     for (int l : layers) shapes.push_back(ctx.layers[l].shape);
     std::sort(shapes.begin(), shapes.end());
-    std::string key = "n" + std::to_string(ldc) + (tc ? "tc" : "") + ":";
+    std::string key = "n" + std::to_string(ldc) + ":";
     for (int s : shapes) key += std::to_string(s) + ",";
     return key;
 }
@@ -411,49 +457,61 @@ template <class C>
 Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols) {
     const bool dbl = sizeof(C) == 16;
     const int ldc = padded_ldc(dbl, ncols);
-    const bool tc = !dbl && ctx.use_tc && tc_columns(ldc) > 0;
-    auto it = ctx.tuned.find(tune_key(ctx, layers, ldc, tc));
-    if (it != ctx.tuned.end()) return get_batch_cfg<C>(ctx, layers, ncols, it->second.first, it->second.second);
+    const bool tc_ok = !dbl && tc_columns(ldc) > 0;
+    auto it = ctx.tuned.find(tune_key(ctx, layers, ldc));
+    if (it != ctx.tuned.end()) {
+        const auto& ch = it->second;
+        return get_batch_cfg<C>(ctx, layers, ncols, ch.KS, ch.CC, tc_ok && ch.tc, ch.KS_tc);
+    }
     // default: split the reductions when the batch alone cannot fill the GPU
     const int nchunks = ldc / chunk_cols(dbl, ncols);
     const int KS = ((long long)layers.size() * nchunks >= 64) ? (1 << 30) : 8;
-    return get_batch_cfg<C>(ctx, layers, ncols, KS, 0);
+    const bool tc = tc_ok && ctx.tc_mode == 1;
+    const int nchunks_tc = tc ? ldc / tc_columns(ldc) : 1;
+    const int KS_tc = ((long long)layers.size() * nchunks_tc >= 32) ? (1 << 30) : ctx.tc_ks;
+    return get_batch_cfg<C>(ctx, layers, ncols, KS, 0, tc, KS_tc);
 }
 
 template <class C>
 void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols) {
     const bool dbl = sizeof(C) == 16;
     const int ldc = padded_ldc(dbl, ncols);
-    const bool tc = !dbl && ctx.use_tc && tc_columns(ldc) > 0;
-    const std::string key = tune_key(ctx, layers, ldc, tc);
+    const bool tc_ok = !dbl && tc_columns(ldc) > 0;
+    const std::string key = tune_key(ctx, layers, ldc);
     if (!ctx.autotune || ctx.tuned.count(key)) return;
     const int cc0 = chunk_cols(dbl, ncols);
-    std::vector<int> ccs{cc0};
-    if (cc0 >= 16 && ldc % (cc0 / 2) == 0) ccs.push_back(cc0 / 2);
-    const int kss[] = {4, 8, 16, 1 << 30};
+    std::vector<Ctx::TuneChoice> cands;
+    if (ctx.tc_mode != 1 || !tc_ok) {
+        std::vector<int> ccs{cc0};
+        if (cc0 >= 16 && ldc % (cc0 / 2) == 0) ccs.push_back(cc0 / 2);
+        for (int cc : ccs)
+            for (int ks : {4, 8, 16, 1 << 30}) cands.push_back({ks, cc, 0, 1 << 30});
+    }
+    if (tc_ok && ctx.tc_mode >= 1)
+        for (int kstc : {4, 16, 1 << 30}) cands.push_back({8, cc0, 1, kstc});
     cudaEvent_t e0, e1;
     HZ_CUDA(cudaEventCreate(&e0));
     HZ_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    std::pair<int, int> choice{1 << 30, cc0};
+    Ctx::TuneChoice choice = cands.front();
     const bool prof = ctx.prof;
     ctx.prof = false;
     std::string log = key + " ->";
-    for (int cc : ccs)
-        for (int ks : kss) {
-            Batch& b = get_batch_cfg<C>(ctx, layers, ncols, ks, cc);
-            for (size_t j = 0; j < b.vec_ptrs.size(); ++j)
-                HZ_CUDA(cudaMemsetAsync(b.vec_ptrs[j].first, 0, (size_t)b.vec_rows[j] * ldc * sizeof(C), ctx.stream));
-            substitute<C>(ctx, b, ncols, ctx.stream);  // warm-up
-            HZ_CUDA(cudaEventRecord(e0, ctx.stream));
-            substitute<C>(ctx, b, ncols, ctx.stream);
-            HZ_CUDA(cudaEventRecord(e1, ctx.stream));
-            HZ_CUDA(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            HZ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            log += " (KS " + std::to_string(ks > 1000 ? 0 : ks) + ", CC " + std::to_string(cc) + ") " + std::to_string(ms) + " ms;";
-            if (ms < best) { best = ms; choice = {ks, cc}; }
-        }
+    for (const auto& cd : cands) {
+        Batch& b = get_batch_cfg<C>(ctx, layers, ncols, cd.KS, cd.CC, cd.tc != 0, cd.KS_tc);
+        for (size_t j = 0; j < b.vec_ptrs.size(); ++j)
+            HZ_CUDA(cudaMemsetAsync(b.vec_ptrs[j].first, 0, (size_t)b.vec_rows[j] * ldc * sizeof(C), ctx.stream));
+        substitute<C>(ctx, b, ncols, ctx.stream);  // warm-up
+        HZ_CUDA(cudaEventRecord(e0, ctx.stream));
+        substitute<C>(ctx, b, ncols, ctx.stream);
+        HZ_CUDA(cudaEventRecord(e1, ctx.stream));
+        HZ_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        HZ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        log += std::string(cd.tc ? " (TC, KS " : " (KS ") + std::to_string((cd.tc ? cd.KS_tc : cd.KS) > 1000 ? 0 : (cd.tc ? cd.KS_tc : cd.KS)) +
+               ", CC " + std::to_string(cd.CC) + ") " + std::to_string(ms) + " ms;";
+        if (ms < best) { best = ms; choice = cd; }
+    }
     ctx.prof = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -462,11 +520,11 @@ void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols) {
 }
 
 template <class C>
-Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS, int CC) {
+Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS, int CC, bool tc, int KS_tc) {
     const bool dbl = sizeof(C) == 16;
     const int ldc = padded_ldc(dbl, ncols);
-    const bool tc = !dbl && ctx.use_tc && tc_columns(ldc) > 0;
-    std::string key = "KS" + std::to_string(KS) + "C" + std::to_string(CC) + "n" + std::to_string(ldc) + (tc ? "tc" : "") + ":";
+    std::string key = "KS" + std::to_string(KS) + "C" + std::to_string(CC) + "n" + std::to_string(ldc) +
+                      (tc ? "tc" + std::to_string(KS_tc) : "") + ":";
     for (int l : layers) key += std::to_string(l) + ",";
     auto it = ctx.batches.find(key);
     if (it != ctx.batches.end()) return it->second;
@@ -475,14 +533,18 @@ Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS
     b.KS = KS;
     b.CC = CC;
     b.tc = tc;
-    const int nchunks_tc = tc ? ldc / tc_columns(ldc) : 1;
-    b.KS_tc = ((long long)layers.size() * nchunks_tc >= 32) ? (1 << 30) : ctx.tc_ks;
+    b.KS_tc = KS_tc;
     int H = 0;
     for (int l : layers) H = std::max(H, (int)ctx.shapes[ctx.layers[l].shape].levels.size());
     b.H = H;
     std::vector<std::vector<Task>> lists[4], quads[4];
     for (auto& v : lists) v.assign(H, {});
     for (auto& v : quads) v.assign(H, {});
+    for (int k = 0; k < 2; ++k)
+        for (int mode = 0; mode < 4; ++mode) {
+            b.lvl_bytes[k][mode].assign(H, 0.0);
+            b.lvl_flops[k][mode].assign(H, 0.0);
+        }
     auto split = [&](std::vector<Task>& out, int j, int nid, int tile, int k0, int k1, int ks) {
         if (k1 <= k0) { out.push_back(Task{j, nid, tile, k0}); return; }
         for (int k = k0; k < k1; k += ks) out.push_back(Task{j, nid, tile, k});
@@ -494,7 +556,13 @@ Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS
                 const Node& nd = sh.nodes[nid];
                 for (int mode = 0; mode < 4; ++mode) {
                     const int out_t = mode == 1 ? nd.upd_t : nd.own_t;
-                    if (tc && tc_node(mode, nd, ctx.tc_min_tiles)) {
+                    const bool on_tc = tc && tc_node(mode, nd, ctx.tc_min_tiles);
+                    // stored factor entries this product reads (triangular L^{-1} or L21)
+                    const double ent = (mode == FA || mode == BB) ? (double)nd.nown * (nd.nown + 1) / 2.0
+                                                                  : (double)nd.nown * nd.nupd;
+                    b.lvl_bytes[on_tc][mode][h] += ent * sizeof(C);
+                    b.lvl_flops[on_tc][mode][h] += 8.0 * ent;
+                    if (on_tc) {
                         for (int t = 0; t < out_t; t += 4) {
                             if (mode == 0) split(quads[0][h], j, nid, t, 0, std::min(t + 4, nd.own_t), b.KS_tc);
                             if (mode == 1) split(quads[1][h], j, nid, t, 0, nd.own_t, b.KS_tc);
@@ -572,8 +640,8 @@ template void substitute<float2>(Ctx&, const Batch&, int, cudaStream_t);
 template void substitute<double2>(Ctx&, const Batch&, int, cudaStream_t);
 template Batch& get_batch<float2>(Ctx&, const std::vector<int>&, int);
 template Batch& get_batch<double2>(Ctx&, const std::vector<int>&, int);
-template Batch& get_batch_cfg<float2>(Ctx&, const std::vector<int>&, int, int, int);
-template Batch& get_batch_cfg<double2>(Ctx&, const std::vector<int>&, int, int, int);
+template Batch& get_batch_cfg<float2>(Ctx&, const std::vector<int>&, int, int, int, bool, int);
+template Batch& get_batch_cfg<double2>(Ctx&, const std::vector<int>&, int, int, int, bool, int);
 template void ensure_tuned<float2>(Ctx&, const std::vector<int>&, int);
 template void ensure_tuned<double2>(Ctx&, const std::vector<int>&, int);
 

@@ -13,16 +13,20 @@
 // FP32-level accuracy (about 2^-21 relative): 12 MMAs (M = 128, N = NT, K = 8) per 8 complex
 // reduction indices.
 //
-// Pipeline (256 threads, 16 complex reduction indices per stage):
-//   raw stage  : cp.async 16-byte copies of the factor tiles and vector rows into shared memory,
-//                two stages ahead; masked rows / absent tiles are zero-filled by the copy;
-//   conversion : shared -> shared, split into hi/lo TF32 operands in the K-major core-matrix
-//                layout (no swizzle), 16-byte conflict-free stores;
-//   MMA        : one thread issues the 24 MMAs of a stage and commits them to an mbarrier that
-//                releases the converted buffer two stages later.
-// The epilogue reads both accumulators from tensor memory (tcgen05.ld; lane = complex row) and
-// accumulates into the solve vectors exactly like the CUDA-core kernel.  Every mbarrier wait is
-// bounded and block-uniform; on timeout the block records an error flag, waits once more
+// Warp-specialized pipeline (416 threads, 16 complex reduction indices per stage, two-deep
+// rings of raw and converted buffers, every hand-off an mbarrier):
+//   4 loader warps    : cp.async 16-byte copies of the factor tiles and vector rows into a raw
+//                       buffer (masked rows / absent tiles zero-filled by the copy), completion
+//                       signalled with cp.async.mbarrier.arrive;
+//   8 converter warps : raw -> split hi/lo TF32 operands in the K-major core-matrix layout
+//                       (no swizzle), 16-byte stores;
+//   1 MMA warp        : one thread issues the 24 MMAs of a stage and commits them to the
+//                       mbarrier that releases the converted buffer.
+// The epilogue (converter warps) stages both accumulators from tensor memory (tcgen05.ld;
+// lane = complex row) through shared memory and writes whole rows with 16-byte accesses: a
+// task that covers the full reduction of its rows stores them, split reductions and the
+// shared update rows of FB accumulate with vector atomics.  Every mbarrier wait is bounded and
+// the outcome block-uniform; on timeout the block records an error flag, waits once more
 // (bounded) for its own MMAs, frees its tensor memory and exits.
 #include <algorithm>
 
@@ -92,19 +96,37 @@ template <int NT> struct Layout {
     static constexpr int RAW_A = 4 * 32 * TROW;          // large enough for both raw tile layouts
     static constexpr int RAW_X = KC * NT * 8;
     static constexpr int RAW = RAW_A + RAW_X;
-    static constexpr int TOTAL = 2 * CONV + 2 * RAW + 64;
+    static constexpr int TOTAL = 2 * CONV + 2 * RAW + 128;
 };
 
+// thread roles (warp-specialized): 4 loader warps, 8 converter warps, 1 MMA warp
+constexpr int NLOAD = 128, NCONVT = 256, NTHREADS = NLOAD + NCONVT + 32;
+
+__device__ inline void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(b)), "r"(count));
+}
+__device__ inline void mbar_arrive(uint64_t* b) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" :: "r"(smem_u32(b)) : "memory");
+}
+// arrive on b once all of this thread's earlier cp.async copies have landed
+__device__ inline void cp_async_arrive(uint64_t* b) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" :: "r"(smem_u32(b)) : "memory");
+}
+
 template <int NT, int MODE>
-__global__ void __launch_bounds__(256, 1) k_subst_tc(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ jobs,
-                                                     int ldc, int nchunks, int KS, int* flag) {
+__global__ void __launch_bounds__(NTHREADS, 1) k_subst_tc(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ jobs,
+                                                          int ldc, int nchunks, int KS, int* flag) {
     using LY = Layout<NT>;
     constexpr bool TR = (MODE == BA || MODE == BB);  // factor tiles used transposed
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* conv = smem;
     unsigned char* raw = smem + 2 * LY::CONV;
     uint64_t* bars = (uint64_t*)(raw + 2 * LY::RAW);
-    uint32_t* tptr = (uint32_t*)(bars + 2);
+    uint64_t* raw_full = bars + 0;    // [2] loaders' copies landed (count NLOAD)
+    uint64_t* raw_empty = bars + 2;   // [2] converters done reading (count NCONVT)
+    uint64_t* conv_full = bars + 4;   // [2] converted operands written (count NCONVT)
+    uint64_t* conv_empty = bars + 6;  // [2] MMAs of the buffer done (tcgen05.commit)
+    uint32_t* tptr = (uint32_t*)(bars + 8);
 
     const int chunk = blockIdx.x % nchunks;
     const Task tk = tasks[blockIdx.x / nchunks];
@@ -115,143 +137,147 @@ __global__ void __launch_bounds__(256, 1) k_subst_tc(const Task* __restrict__ ta
     const int o0 = tk.tile;  // first of the four output tiles
     const int nout_t = (MODE == FB) ? nd.upd_t : nd.own_t;
     const int kbeg = tk.pad_;
-    int kend = (MODE == FA) ? min(o0 + 4, nd.own_t) : ((MODE == BA) ? nd.upd_t : nd.own_t);
-    kend = min(kend, kbeg + KS);
+    const int kend = min((MODE == FA) ? min(o0 + 4, nd.own_t) : ((MODE == BA) ? nd.upd_t : nd.own_t), kbeg + KS);
     const int nst = max(0, kend - kbeg) * 2;
     const float2* vec = (MODE == FA || MODE == BB) ? jb.acc : jb.x;
     const int* upd = jb.upd_idx + nd.upd_off;
     const int nrows_k = (MODE == BA) ? nd.nupd : nd.nown;   // valid vector rows
+    const int mma_warp = (NLOAD + NCONVT) / 32;
 
-    // issue the raw copies of stage s into raw buffer s % 2 (all threads)
-    auto load_raw = [&](int s) {
-        if (s >= nst) return;
-        unsigned char* rb = raw + (s & 1) * LY::RAW;
-        const int kt = kbeg + (s >> 1), hk = s & 1;
-        // factor tiles: 4 output tiles x 16 reduction indices = 1024 chunks of 16 bytes
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int c = t + 256 * i;
-            const int oi = c >> 8, q = c & 255;
-            const int o = o0 + oi;
-            bool exists = o < nout_t;
-            if (MODE == FA) exists = exists && kt <= o;
-            if (MODE == BB) exists = exists && kt >= o;
-            long long toff = 0;
-            if (exists) {
-                if (MODE == FA) toff = nd.linv_off + tri_idx(o, kt);
-                else if (MODE == FB) toff = nd.l21_off + (long long)o * nd.own_t + kt;
-                else if (MODE == BA) toff = nd.l21_off + (long long)kt * nd.own_t + o;
-                else toff = nd.linv_off + tri_idx(kt, o);
-            }
-            const float2* tl = jb.fac + toff * TILE2;
-            uint32_t dst;
-            const float2* src;
-            if (!TR) {  // stored (r, k) at r + 32 k: columns 16 hk .. +16 are contiguous; raw [oi][k][r]
-                dst = smem_u32(rb + oi * 4096 + q * 16);
-                src = tl + hk * KC * 32 + q * 2;
-            } else {    // stored (k, r) at k + 32 r: row r's 16 entries are contiguous; raw [oi][r][k], 144 B rows
-                const int r = q >> 3, j = q & 7;
-                dst = smem_u32(rb + oi * 32 * TROW + r * TROW + j * 16);
-                src = tl + 32 * r + hk * KC + j * 2;
-            }
-            cp16(dst, exists ? (const void*)src : (const void*)jb.fac, exists ? 16 : 0);
-        }
-        // vector rows: KC rows x NT columns, raw [k][n]
-        for (int c = t; c < KC * NT / 2; c += 256) {
-            const int k = c / (NT / 2), j = c % (NT / 2);
-            const int rr = kt * TILE + hk * KC + k;
-            const bool v = rr < nrows_k;
-            long long row = 0;
-            if (v) row = (MODE == BA) ? (long long)upd[rr] : (long long)(nd.own0 + rr);
-            const float2* src = vec + row * ldc + col0 + 2 * j;
-            cp16(smem_u32(rb + LY::RAW_A + k * NT * 8 + j * 16), src, v ? 16 : 0);
-        }
-    };
-
-    if (w == 0) {
+    if (w == mma_warp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(tptr)), "r"(2 * NT));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (t == 0)
-        for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bars + b)), "r"(1));
-    load_raw(0);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    load_raw(1);
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    if (t == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(raw_full + b, NLOAD);
+            mbar_init(raw_empty + b, NCONVT);
+            mbar_init(conv_full + b, NCONVT);
+            mbar_init(conv_empty + b, 1);
+        }
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tptr;
     const uint32_t tm_r = tmem, tm_i = tmem + NT;  // accumulators: real part cols [0, NT), imag [NT, 2NT)
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(MR >> 4) << 24);
-    const uint32_t idesc_neg = idesc | (1u << 13);
-
     bool ok = true;
-    for (int s = 0; s < nst; ++s) {
-        const int cb = s & 1;
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-        __syncthreads();  // raw stage s complete for every thread
-        if (s >= 2) {     // converted buffer cb is free once the MMAs of stage s-2 are done
-            const bool got = mbar_wait(smem_u32(bars + cb), (uint32_t)(((s >> 1) - 1) & 1));
-            ok = __syncthreads_and(got) != 0;
+
+    if (t < NLOAD) {
+        // ------------------------------------------------------------ loaders
+        for (int s = 0; s < nst && ok; ++s) {
+            const int slot = s & 1;
+            if (s >= 2) ok = mbar_wait(smem_u32(raw_empty + slot), (uint32_t)(((s >> 1) - 1) & 1));
             if (!ok) break;
-        }
-        unsigned char* rb = raw + cb * LY::RAW;
-        unsigned char* cv = conv + cb * LY::CONV;
-        // ---- convert factor operand: 128 rows x 16 k, thread -> (row, 4 consecutive k)
+            unsigned char* rb = raw + slot * LY::RAW;
+            const int kt = kbeg + (s >> 1), hk = s & 1;
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int id = t + 256 * i;
-            const int row = id & 127, kq = id >> 7;
-            const int oi = row >> 5, r = row & 31;
-            float re[4], im[4];
-            if (!TR) {
-                const float2* src = (const float2*)(rb + oi * 4096);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) { float2 a = src[(4 * kq + j) * 32 + r]; re[j] = a.x; im[j] = a.y; }
-            } else {
-                const float4* src = (const float4*)(rb + oi * 32 * TROW + r * TROW + kq * 32);
-                float4 a0 = src[0], a1 = src[1];
-                re[0] = a0.x; im[0] = a0.y; re[1] = a0.z; im[1] = a0.w;
-                re[2] = a1.x; im[2] = a1.y; re[3] = a1.z; im[3] = a1.w;
+            for (int i = 0; i < 8; ++i) {     // factor tiles: 1024 chunks of 16 bytes
+                const int c = t + NLOAD * i;
+                const int oi = c >> 8, q = c & 255;
+                const int o = o0 + oi;
+                bool exists = o < nout_t;
+                if (MODE == FA) exists = exists && kt <= o;
+                if (MODE == BB) exists = exists && kt >= o;
+                long long toff = 0;
+                if (exists) {
+                    if (MODE == FA) toff = nd.linv_off + tri_idx(o, kt);
+                    else if (MODE == FB) toff = nd.l21_off + (long long)o * nd.own_t + kt;
+                    else if (MODE == BA) toff = nd.l21_off + (long long)kt * nd.own_t + o;
+                    else toff = nd.linv_off + tri_idx(kt, o);
+                }
+                const float2* tl = jb.fac + toff * TILE2;
+                uint32_t dst;
+                const float2* src;
+                if (!TR) {
+                    dst = smem_u32(rb + oi * 4096 + q * 16);
+                    src = tl + hk * KC * 32 + q * 2;
+                } else {
+                    const int r = q >> 3, j = q & 7;
+                    dst = smem_u32(rb + oi * 32 * TROW + r * TROW + j * 16);
+                    src = tl + 32 * r + hk * KC + j * 2;
+                }
+                cp16(dst, exists ? (const void*)src : (const void*)jb.fac, exists ? 16 : 0);
             }
-            float4 rh, rl, ih, il;
-            rh.x = tf32_hi(re[0]); rh.y = tf32_hi(re[1]); rh.z = tf32_hi(re[2]); rh.w = tf32_hi(re[3]);
-            ih.x = tf32_hi(im[0]); ih.y = tf32_hi(im[1]); ih.z = tf32_hi(im[2]); ih.w = tf32_hi(im[3]);
-            rl = make_float4(re[0] - rh.x, re[1] - rh.y, re[2] - rh.z, re[3] - rh.w);
-            il = make_float4(im[0] - ih.x, im[1] - ih.y, im[2] - ih.z, im[3] - ih.w);
-            const int off = coff(row, 4 * kq);
-            *(float4*)(cv + 0 * LY::A_MAT + off) = rh;
-            *(float4*)(cv + 1 * LY::A_MAT + off) = rl;
-            *(float4*)(cv + 2 * LY::A_MAT + off) = ih;
-            *(float4*)(cv + 3 * LY::A_MAT + off) = il;
+            for (int c = t; c < KC * NT / 2; c += NLOAD) {  // vector rows: KC x NT, raw [k][n]
+                const int k = c / (NT / 2), j = c % (NT / 2);
+                const int rr = kt * TILE + hk * KC + k;
+                const bool v = rr < nrows_k;
+                long long row = 0;
+                if (v) row = (MODE == BA) ? (long long)upd[rr] : (long long)(nd.own0 + rr);
+                cp16(smem_u32(rb + LY::RAW_A + k * NT * 8 + j * 16), vec + row * ldc + col0 + 2 * j, v ? 16 : 0);
+            }
+            cp_async_arrive(raw_full + slot);
         }
-        // ---- convert vector operand: NT rows (columns n) x 16 k
-        for (int id = t; id < NT * 4; id += 256) {
-            const int n = id % NT, kq = id / NT;
-            const float2* src = (const float2*)(rb + LY::RAW_A);
-            float re[4], im[4];
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (t < NLOAD + NCONVT) {
+        // ------------------------------------------------------------ converters
+        const int ct = t - NLOAD;
+        for (int s = 0; s < nst && ok; ++s) {
+            const int slot = s & 1;
+            ok = mbar_wait(smem_u32(raw_full + slot), (uint32_t)((s >> 1) & 1));
+            if (ok && s >= 2) ok = mbar_wait(smem_u32(conv_empty + slot), (uint32_t)(((s >> 1) - 1) & 1));
+            if (!ok) break;
+            unsigned char* rb = raw + slot * LY::RAW;
+            unsigned char* cv = conv + slot * LY::CONV;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) { float2 a = src[(4 * kq + j) * NT + n]; re[j] = a.x; im[j] = a.y; }
-            float4 rh, rl, ih, il;
-            rh.x = tf32_hi(re[0]); rh.y = tf32_hi(re[1]); rh.z = tf32_hi(re[2]); rh.w = tf32_hi(re[3]);
-            ih.x = tf32_hi(im[0]); ih.y = tf32_hi(im[1]); ih.z = tf32_hi(im[2]); ih.w = tf32_hi(im[3]);
-            rl = make_float4(re[0] - rh.x, re[1] - rh.y, re[2] - rh.z, re[3] - rh.w);
-            il = make_float4(im[0] - ih.x, im[1] - ih.y, im[2] - ih.z, im[3] - ih.w);
-            const int off = 4 * LY::A_MAT + coff(n, 4 * kq);
-            *(float4*)(cv + off + 0 * LY::X_MAT) = rh;
-            *(float4*)(cv + off + 1 * LY::X_MAT) = rl;
-            *(float4*)(cv + off + 2 * LY::X_MAT) = ih;
-            *(float4*)(cv + off + 3 * LY::X_MAT) = il;
+            for (int i = 0; i < 2; ++i) {     // factor operand: 128 rows x 16 k, (row, 4 consecutive k)
+                const int id = ct + NCONVT * i;
+                const int row = id & 127, kq = id >> 7;
+                const int oi = row >> 5, r = row & 31;
+                float re[4], im[4];
+                if (!TR) {
+                    const float2* src = (const float2*)(rb + oi * 4096);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) { float2 a = src[(4 * kq + j) * 32 + r]; re[j] = a.x; im[j] = a.y; }
+                } else {
+                    const float4* src = (const float4*)(rb + oi * 32 * TROW + r * TROW + kq * 32);
+                    float4 a0 = src[0], a1 = src[1];
+                    re[0] = a0.x; im[0] = a0.y; re[1] = a0.z; im[1] = a0.w;
+                    re[2] = a1.x; im[2] = a1.y; re[3] = a1.z; im[3] = a1.w;
+                }
+                float4 rh, rl, ih, il;
+                rh.x = tf32_hi(re[0]); rh.y = tf32_hi(re[1]); rh.z = tf32_hi(re[2]); rh.w = tf32_hi(re[3]);
+                ih.x = tf32_hi(im[0]); ih.y = tf32_hi(im[1]); ih.z = tf32_hi(im[2]); ih.w = tf32_hi(im[3]);
+                rl = make_float4(re[0] - rh.x, re[1] - rh.y, re[2] - rh.z, re[3] - rh.w);
+                il = make_float4(im[0] - ih.x, im[1] - ih.y, im[2] - ih.z, im[3] - ih.w);
+                const int off = coff(row, 4 * kq);
+                *(float4*)(cv + 0 * LY::A_MAT + off) = rh;
+                *(float4*)(cv + 1 * LY::A_MAT + off) = rl;
+                *(float4*)(cv + 2 * LY::A_MAT + off) = ih;
+                *(float4*)(cv + 3 * LY::A_MAT + off) = il;
+            }
+            for (int id = ct; id < NT * 4; id += NCONVT) {   // vector operand: NT rows x 16 k
+                const int n = id % NT, kq = id / NT;
+                const float2* src = (const float2*)(rb + LY::RAW_A);
+                float re[4], im[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) { float2 a = src[(4 * kq + j) * NT + n]; re[j] = a.x; im[j] = a.y; }
+                float4 rh, rl, ih, il;
+                rh.x = tf32_hi(re[0]); rh.y = tf32_hi(re[1]); rh.z = tf32_hi(re[2]); rh.w = tf32_hi(re[3]);
+                ih.x = tf32_hi(im[0]); ih.y = tf32_hi(im[1]); ih.z = tf32_hi(im[2]); ih.w = tf32_hi(im[3]);
+                rl = make_float4(re[0] - rh.x, re[1] - rh.y, re[2] - rh.z, re[3] - rh.w);
+                il = make_float4(im[0] - ih.x, im[1] - ih.y, im[2] - ih.z, im[3] - ih.w);
+                const int off = 4 * LY::A_MAT + coff(n, 4 * kq);
+                *(float4*)(cv + off + 0 * LY::X_MAT) = rh;
+                *(float4*)(cv + off + 1 * LY::X_MAT) = rl;
+                *(float4*)(cv + off + 2 * LY::X_MAT) = ih;
+                *(float4*)(cv + off + 3 * LY::X_MAT) = il;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(raw_empty + slot);
+            mbar_arrive(conv_full + slot);
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();  // conversion visible to the tensor core; raw buffer cb free
-        load_raw(s + 2);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        if (t == 0) {
+    } else if (l == 0) {
+        // ------------------------------------------------------------ MMA issuer
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(MR >> 4) << 24);
+        const uint32_t idesc_neg = idesc | (1u << 13);
+        for (int s = 0; s < nst && ok; ++s) {
+            const int cb = s & 1;
+            ok = mbar_wait(smem_u32(conv_full + cb), (uint32_t)((s >> 1) & 1));
+            if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t base = smem_u32(cv);
+            const uint32_t base = smem_u32(conv + cb * LY::CONV);
 #pragma unroll
             for (int ks = 0; ks < KC / 8; ++ks) {
                 const uint32_t ko = ks * 2 * LBO;
@@ -261,15 +287,13 @@ __global__ void __launch_bounds__(256, 1) k_subst_tc(const Task* __restrict__ ta
                 const uint64_t xrh = smem_desc(xb), xrl = smem_desc(xb + LY::X_MAT);
                 const uint64_t xih = smem_desc(xb + 2 * LY::X_MAT), xil = smem_desc(xb + 3 * LY::X_MAT);
                 const uint32_t first = (s == 0 && ks == 0) ? 0u : 1u;
-                // Yr = Ar Xr - Ai Xi
-                mma_tf32(tm_r, arh, xrh, idesc, first);
+                mma_tf32(tm_r, arh, xrh, idesc, first);      // Yr = Ar Xr - Ai Xi
                 mma_tf32(tm_r, arh, xrl, idesc, 1u);
                 mma_tf32(tm_r, arl, xrh, idesc, 1u);
                 mma_tf32(tm_r, aih, xih, idesc_neg, 1u);
                 mma_tf32(tm_r, aih, xil, idesc_neg, 1u);
                 mma_tf32(tm_r, ail, xih, idesc_neg, 1u);
-                // Yi = Ai Xr + Ar Xi
-                mma_tf32(tm_i, aih, xrh, idesc, first);
+                mma_tf32(tm_i, aih, xrh, idesc, first);      // Yi = Ai Xr + Ar Xi
                 mma_tf32(tm_i, aih, xrl, idesc, 1u);
                 mma_tf32(tm_i, ail, xrh, idesc, 1u);
                 mma_tf32(tm_i, arh, xih, idesc, 1u);
@@ -277,62 +301,110 @@ __global__ void __launch_bounds__(256, 1) k_subst_tc(const Task* __restrict__ ta
                 mma_tf32(tm_i, arl, xih, idesc, 1u);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(smem_u32(bars + cb)));
+                         :: "r"(smem_u32(conv_empty + cb)));
         }
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    if (ok && nst > 0) {
-        const bool got = mbar_wait(smem_u32(bars + ((nst - 1) & 1)), (uint32_t)(((nst - 1) >> 1) & 1));
-        ok = __syncthreads_and(got) != 0;
+
+    // every role arrives here (their waits are bounded); make the outcome block-uniform
+    ok = __syncthreads_and(ok) != 0;
+    bool done = true;
+    if (nst > 0) {
+        const bool got = mbar_wait(smem_u32(conv_empty + ((nst - 1) & 1)), (uint32_t)(((nst - 1) >> 1) & 1));
+        done = __syncthreads_and(got) != 0;
     }
-    if (!ok) {
+    if (!ok || !done) {
         if (t == 0) atomicExch(flag, 1);
-        if (nst > 0) mbar_wait(smem_u32(bars + ((nst - 1) & 1)), (uint32_t)(((nst - 1) >> 1) & 1));
+        ok = false;
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-    // ---- epilogue: warp w reads lanes 32 (w % 4) .. +31 (= output tile o0 + w % 4), column half w / 4
-    if (ok) {
-        const int q4 = w & 3;
-        const int row = (o0 + q4) * TILE + l;
-        const bool valid = (o0 + q4) < nout_t && row < ((MODE == FB) ? nd.nupd : nd.nown);
-        const int cbeg = (w >> 2) * (NT / 2);
-        for (int c0 = cbeg; c0 < cbeg + NT / 2; c0 += 16) {
-            uint32_t vr[16], vi[16];
-            if (nst > 0) {
-                const uint32_t lane_off = (uint32_t)(32 * q4) << 16;
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                             : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]), "=r"(vr[7]),
-                               "=r"(vr[8]), "=r"(vr[9]), "=r"(vr[10]), "=r"(vr[11]), "=r"(vr[12]), "=r"(vr[13]), "=r"(vr[14]), "=r"(vr[15])
-                             : "r"(tm_r + lane_off + (uint32_t)c0));
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                             : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]), "=r"(vi[7]),
-                               "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]), "=r"(vi[13]), "=r"(vi[14]), "=r"(vi[15])
-                             : "r"(tm_i + lane_off + (uint32_t)c0));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            } else {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) { vr[j] = 0u; vi[j] = 0u; }
-            }
-            if (!valid) continue;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                float2 y = make_float2(__uint_as_float(vr[j]), __uint_as_float(vi[j]));
-                const int col = col0 + c0 + j;
-                if (MODE == FB) {
-                    atomicAdd(jb.acc + (long long)upd[row] * ldc + col, make_float2(-y.x, -y.y));
+    // ---- epilogue (converter warps), in two passes so that global memory sees whole rows:
+    //  (1) tensor memory -> shared staging tile [128 rows][NT + 2] (warp w reads lanes
+    //      32 (w % 4) .. +31 = output tile o0 + w % 4, column half by the converter-warp index);
+    //  (2) each converter warp writes 16 staged rows, lane = pair of columns (16-byte accesses).
+    //  A task that covers the whole reduction of its outputs is their only writer and stores;
+    //  split reductions (and FB, whose update rows are shared between nodes) accumulate.
+    if (ok && t >= NLOAD && t < NLOAD + NCONVT) {
+        constexpr int SP = NT + 2;           // staging pitch (complex): 16-byte rows, odd in 16-byte units
+        float2* stg = (float2*)smem;         // operand and raw buffers are free once the MMAs are done
+        const int cw = (t - NLOAD) >> 5;     // converter warp 0..7
+        {
+            const int q4 = w & 3;
+            const int rl = 32 * q4 + l;
+            const int cbeg = (cw >> 2) * (NT / 2);
+            for (int c0 = cbeg; c0 < cbeg + NT / 2; c0 += 16) {
+                uint32_t vr[16], vi[16];
+                if (nst > 0) {
+                    const uint32_t lane_off = (uint32_t)(32 * q4) << 16;
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                                 : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]), "=r"(vr[7]),
+                                   "=r"(vr[8]), "=r"(vr[9]), "=r"(vr[10]), "=r"(vr[11]), "=r"(vr[12]), "=r"(vr[13]), "=r"(vr[14]), "=r"(vr[15])
+                                 : "r"(tm_r + lane_off + (uint32_t)c0));
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                                 : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]), "=r"(vi[7]),
+                                   "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]), "=r"(vi[13]), "=r"(vi[14]), "=r"(vi[15])
+                                 : "r"(tm_i + lane_off + (uint32_t)c0));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 } else {
-                    const long long eidx = (long long)(nd.own0 + row) * ldc + col;
-                    if (MODE == FA || MODE == BB) {
-                        atomicAdd(jb.x + eidx, y);
-                    } else {  // BA: acc += Dinv z - partial; the first split clears z
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) { vr[j] = 0u; vi[j] = 0u; }
+                }
+#pragma unroll
+                for (int j = 0; j < 16; j += 2)
+                    *(float4*)&stg[rl * SP + c0 + j] = make_float4(__uint_as_float(vr[j]), __uint_as_float(vi[j]),
+                                                                   __uint_as_float(vr[j + 1]), __uint_as_float(vi[j + 1]));
+            }
+        }
+        asm volatile("bar.sync 1, %0;" :: "n"(NCONVT) : "memory");   // converter warps only
+
+        const int kfull0 = (MODE == BB) ? o0 : 0;
+        const int kfull1 = (MODE == FA) ? min(o0 + 4, nd.own_t) : ((MODE == BA) ? nd.upd_t : nd.own_t);
+        const bool unique = kbeg == kfull0 && kend == kfull1 && MODE != FB;
+        const int nrows_out = (MODE == FB) ? nd.nupd : nd.nown;
+        constexpr int RB = 4, NV = NT / 64;  // rows per batch; 16-byte column pairs per lane and row
+        for (int i0 = 0; i0 < 16; i0 += RB) {
+            long long base[RB];
+            bool vrow[RB];
+            float2 di[RB];
+            float4 z[RB][NV];
+            // all loads of the batch first (row indices, D^{-1}, z), then the writes
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                const int rl2 = cw * 16 + i0 + r;
+                const int row = o0 * TILE + rl2;
+                vrow[r] = (o0 + (rl2 >> 5)) < nout_t && row < nrows_out;
+                base[r] = 0;
+                if (vrow[r]) base[r] = ((MODE == FB) ? (long long)upd[row] : (long long)(nd.own0 + row)) * ldc + col0;
+                if (MODE == BA && kbeg == 0 && vrow[r]) {
+                    di[r] = jb.dinv[nd.own0 + row];
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) z[r][v] = *(const float4*)(jb.x + base[r] + 2 * l + 64 * v);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                if (!vrow[r]) continue;
+                const int rl2 = cw * 16 + i0 + r;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const int c = 2 * l + 64 * v;
+                    float4 y = *(const float4*)&stg[rl2 * SP + c];
+                    if (MODE == FB) {
+                        atomicAdd((float4*)(jb.acc + base[r] + c), make_float4(-y.x, -y.y, -y.z, -y.w));
+                    } else if (MODE == FA || MODE == BB) {
+                        if (unique) *(float4*)(jb.x + base[r] + c) = y;
+                        else atomicAdd((float4*)(jb.x + base[r] + c), y);
+                    } else {  // BA: acc = Dinv z - partial; the first split clears z
                         if (kbeg == 0) {
-                            const float2 di = jb.dinv[nd.own0 + row];
-                            const float2 z = jb.x[eidx];
-                            y = csub(y, cmul(di, z));
-                            jb.x[eidx] = make_float2(0.f, 0.f);
+                            const float2 d = di[r];
+                            const float4 q = z[r][v];
+                            y.x -= d.x * q.x - d.y * q.y; y.y -= d.x * q.y + d.y * q.x;
+                            y.z -= d.x * q.z - d.y * q.w; y.w -= d.x * q.w + d.y * q.z;
+                            *(float4*)(jb.x + base[r] + c) = make_float4(0.f, 0.f, 0.f, 0.f);
                         }
-                        atomicAdd(jb.acc + eidx, make_float2(-y.x, -y.y));
+                        const float4 ny = make_float4(-y.x, -y.y, -y.z, -y.w);
+                        if (unique) *(float4*)(jb.acc + base[r] + c) = ny;
+                        else atomicAdd((float4*)(jb.acc + base[r] + c), ny);
                     }
                 }
             }
@@ -340,7 +412,7 @@ __global__ void __launch_bounds__(256, 1) k_subst_tc(const Task* __restrict__ ta
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(2 * NT));
+    if (w == mma_warp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(2 * NT));
 }
 
 template <int NT, int MODE>
@@ -351,7 +423,7 @@ void launch_one(const Task* tasks, long long n, const JobDev<float2>* jobs, int 
         attr = true;
     }
     const int nchunks = ldc / NT;
-    k_subst_tc<NT, MODE><<<(unsigned)(n * nchunks), 256, Layout<NT>::TOTAL, st>>>(tasks, jobs, ldc, nchunks, KS, flag);
+    k_subst_tc<NT, MODE><<<(unsigned)(n * nchunks), NTHREADS, Layout<NT>::TOTAL, st>>>(tasks, jobs, ldc, nchunks, KS, flag);
     HZ_CHECK_LAUNCH();
 }
 

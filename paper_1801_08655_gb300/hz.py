@@ -27,7 +27,7 @@ EXPORTED = [
     "hz_default_opts", "hz_create", "hz_factor", "hz_solve", "hz_solve_host", "hz_destroy", "hz_last_error",
     "hz_layer_info", "hz_factor_stats", "hz_layer_solve_cost", "hz_layer_solve", "hz_polarized_rhs",
     "hz_apply_mpol", "hz_apply_precond", "hz_reconstruct", "hz_volume_residual",
-    "hz_profile_begin", "hz_profile_end", "hz_kernel_launches", "hz_volume_residual_noalloc",
+    "hz_profile_begin", "hz_profile_begin_detail", "hz_profile_end", "hz_profile_kernel", "hz_kernel_launches", "hz_volume_residual_noalloc",
     "hz_tuning_report", "hz_solve_group", "hz_create_shared",
 ]
 
@@ -88,7 +88,9 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.hz_volume_residual.argtypes = [VP, VP, VP, I32, VP, P(D)]
     lib.hz_volume_residual_noalloc.argtypes = [VP, VP, VP, I32, VP, P(D)]
     lib.hz_profile_begin.argtypes = [VP]
+    lib.hz_profile_begin_detail.argtypes = [VP]
     lib.hz_profile_end.argtypes = [VP, P(ct.c_int64), P(D), P(D), P(D)]
+    lib.hz_profile_kernel.argtypes = [VP, I32, P(ct.c_int64), P(D), P(D), P(D)]
     lib.hz_kernel_launches.argtypes = []
     lib.hz_tuning_report.argtypes = [VP]
     lib.hz_create_shared.argtypes = [VP, VP, P(VP)]
@@ -266,8 +268,15 @@ class Solver:
     def tuning_report(self) -> str:
         return self.lib.hz_tuning_report(self.h).decode()
 
-    def profile_begin(self):
-        self._check(self.lib.hz_profile_begin(self.h))
+    def profile_begin(self, detail: bool = False):
+        fn = self.lib.hz_profile_begin_detail if detail else self.lib.hz_profile_begin
+        self._check(fn(self.h))
+
+    def profile_kernel(self, kind: int):
+        """Per-kernel-kind totals of the last detail-profiled interval: 0 CUDA-core, 1 tensor-core."""
+        n, ms, by, fl = ct.c_int64(), ct.c_double(), ct.c_double(), ct.c_double()
+        self._check(self.lib.hz_profile_kernel(self.h, kind, ct.byref(n), ct.byref(ms), ct.byref(by), ct.byref(fl)))
+        return dict(launches=n.value, ms=ms.value, bytes=by.value, flops=fl.value)
 
     def profile_end(self):
         n, ms, by, fl = ct.c_int64(), ct.c_double(), ct.c_double(), ct.c_double()

@@ -224,6 +224,7 @@ def test_tensor_core_layer_solve(hz, ncols, monkeypatch):
     the tcgen05 kernel (split TF32); they must match the local direct solve within the stage
     tolerance."""
     monkeypatch.setenv("HZ_SUBST_TC", "1")
+    monkeypatch.setenv("HZ_TC_MIN_TILES", "3")   # small fronts too: partial quads, masked rows
     p = W.config(1)
     s = make_solver(hz, p, "mixed")
     parts = D.layer_partition(p.n, p.npml, p.n_layers)
@@ -242,6 +243,7 @@ def test_tensor_core_layer_solve(hz, ncols, monkeypatch):
 def test_tensor_core_polarized_stages(hz, small_case, monkeypatch):
     """M_pol on 4R = 128 stacked columns takes the tensor-core path when it is enabled."""
     monkeypatch.setenv("HZ_SUBST_TC", "1")
+    monkeypatch.setenv("HZ_TC_MIN_TILES", "3")
     p, M = small_case
     s = make_solver(hz, p, "mixed")
     rng = np.random.default_rng(21)
@@ -257,16 +259,45 @@ def test_tensor_core_polarized_stages(hz, small_case, monkeypatch):
 
 
 def test_tensor_core_and_cuda_core_paths_agree(hz, monkeypatch):
+    """Forced tensor-core substitution, forced CUDA-core substitution and the autotuned choice
+    between them (the default) give the same refined solution."""
     p = W.config(2)
     f = p.rhs()
     outs = []
-    for flag in ("1", "0"):
+    for flag in ("1", "0", "2"):
         monkeypatch.setenv("HZ_SUBST_TC", flag)
         s = make_solver(hz, p, "mixed")
         u, info, _ = s.solve(cuda(f))
         outs.append(u.cpu().numpy())
+        if flag == "2":
+            # the tuner timed tensor-core candidates for the batches wide enough for them
+            assert "(TC, KS" in s.tuning_report()
         s.close()
     assert rel(outs[0], outs[1]) < 1e-8
+    assert rel(outs[2], outs[1]) < 1e-8
+
+
+def test_profile_detail_attributes_launches_by_kernel_kind(hz, small_case, monkeypatch):
+    """Detail profiling times every substitution launch and attributes it to the CUDA-core or
+    the tensor-core kernel; the algorithmic flops of the two kinds add up to those of the
+    substitution calls."""
+    monkeypatch.setenv("HZ_SUBST_TC", "1")
+    monkeypatch.setenv("HZ_TC_MIN_TILES", "3")
+    p, M = small_case
+    s = make_solver(hz, p, "mixed")
+    R = 32
+    x = cuda(np.random.default_rng(5).standard_normal(s.trace_shape(R)) + 0j)
+    s.apply_mpol(x)
+    s.profile_begin(detail=True)
+    s.apply_mpol(x)
+    tot = s.profile_end()
+    k0, k1 = s.profile_kernel(0), s.profile_kernel(1)
+    assert tot["calls"] > 0 and k0["launches"] > 0 and k1["launches"] > 0
+    assert k0["ms"] > 0 and k1["ms"] > 0
+    assert abs(k0["flops"] + k1["flops"] - tot["flops"]) <= 0.05 * tot["flops"]
+    with pytest.raises(RuntimeError):
+        s.profile_kernel(2)
+    s.close()
 
 
 def test_graph_replay_matches_direct_launches(hz, monkeypatch):
