@@ -243,9 +243,11 @@ def run_ours(args):
     pk, pk_kind = peaks()
     s.profile_begin(detail=True)
     ep0, ep1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("profile_step")   # lets ncu --nvtx-include select this solve
     ep0.record(stream)
     s.solve(rhs, opts, u=u)
     ep1.record(stream)
+    torch.cuda.nvtx.range_pop()
     prof = s.profile_end()
     stream.synchronize()
     prof_step_ms = ep0.elapsed_time(ep1)
@@ -330,6 +332,7 @@ def run_ours(args):
                        (f"{n}^3 {W.CONFIG_NAMES[args.config]}, R={R}, mixed precision"),
                        "n": n, "layers": p.n_layers, "R": R, "precision": "mixed",
                        "l2": "inputs larger than L2: ~40 GB of factors streamed every GMRES iteration",
+                       "precond_tf32_terms": 1 if os.environ.get("HZ_PRECOND_SPLIT", "3") == "1" else 3,
                        "parallelism": f"replicas x{ws}"},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "per": f"batch of {R} right-hand sides"},

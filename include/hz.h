@@ -101,6 +101,14 @@ void hz_default_opts(hz_precision prec, hz_solve_opts* opts);
  *   stream    cudaStream_t to queue work on (0 for the default stream)
  *   out       receives the new handle (NULL on failure)
  * Errors: HZ_ERR_ARG, HZ_ERR_NONFINITE (m), HZ_ERR_OOM, HZ_ERR_CUDA.
+ * Environment variables read here (they change speed, never the solution beyond rounding):
+ *   HZ_SUBST_TC       complex64 substitutions on the tcgen05 kernel: 0 never, 1 always (for
+ *                     column blocks of >= 64), 2 (default) when the autotuner times it faster
+ *   HZ_TC_MIN_TILES   default minimum output tiles of a tensor-core product (8)
+ *   HZ_PRECOND_SPLIT  1: single-term TF32 tensor-core products inside the preconditioner
+ *                     (default 3 terms, FP32-level)
+ *   HZ_AUTOTUNE=0     keep the fixed defaults; HZ_GRAPHS=0 no CUDA-graph replay;
+ *   HZ_LEAF           nested-dissection leaf size (cells, default 64)
  */
 hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz_pml* pml,
                     int32_t n_layers, hz_precision prec, void* stream, hz_handle** out);

@@ -35,6 +35,8 @@ struct Batch {
     bool tc = false;                            // holds tensor-core task lists (large nodes)
     std::vector<long long> off[4], cnt[4];      // per phase (FA, FB, BA, BB) and level, into d_tasks
     int KS_tc = 1 << 30;                        // split-K of the tensor-core tasks (tiles)
+    int min_t = 8;                              // output tiles a node product needs for the tensor cores
+    int split = 3;                              // TF32 terms per real product on the tensor cores (3 or 1)
     std::vector<long long> pair_off[4], pair_cnt[4];  // tensor-core tasks: two output tiles each
     Task* d_tasks = nullptr;
     void* d_jobs = nullptr;                     // JobDev<C>[njobs]
@@ -169,13 +171,14 @@ struct Ctx {
     std::map<long long, std::unique_ptr<Rec>> plans;   // matvec plans by column count
     // autotuner: (shape signature, ldc) -> chosen split-K depth and column chunk
     bool autotune = true;
-    struct TuneChoice { int KS, CC, tc, KS_tc; };
+    struct TuneChoice { int KS, CC, tc, KS_tc, min_t; };
     std::map<std::string, TuneChoice> tuned;
     std::vector<std::string> tune_log;
     int tc_mode = 2;        // tensor-core substitution (complex64, >= 64 columns): 0 never, 1 always,
                             // 2 when the autotuner measures it faster for the batch signature
     int tc_ks = 4;          // split-K (factor tiles per block) of small tensor-core batches
     int tc_min_tiles = 8;   // output tiles a node product needs to run on the tensor cores
+    int precond_split = 3;  // TF32 terms of the tensor-core products inside the preconditioner (3 or 1)
     std::vector<ProfRec> prof_recs;
     bool prof_detail = false;                 // also time every substitution launch by kernel kind
     std::vector<ProfRec> prof_launch;

@@ -12,13 +12,13 @@ void launch_level_tc(const Batch& b, int h, int mode, int ldc, int* flag, cudaSt
 int padded_ldc(bool is_double, int ncols);
 
 // Job set with per-level task lists, cached by layer list.
-template <class C> Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols);
+template <class C> Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols, int split = 3);
 // Build (or fetch) a batch with an explicit split-K depth and column chunk.
 template <class C> Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS, int CC, bool tc,
-                                       int KS_tc);
+                                       int KS_tc, int min_t, int split = 3);
 // Autotune the substitution of this batch signature (times candidate split-K depths and column
 // chunks on zeroed slot vectors); a no-op once the signature is tuned or when tuning is off.
-template <class C> void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols);
+template <class C> void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols, int split = 3);
 void free_batches(Ctx& ctx);
 
 // Forward/backward substitution for every job of the batch on ncols columns of the

@@ -444,10 +444,13 @@ void rec_zero_slots(Ctx& ctx, Rec& rec, const std::vector<int>& layers, int ldc)
     }
 }
 
+// approx: the substitution serves the preconditioner, whose tensor-core products then run with
+// the handle's precond_split TF32 terms
 template <class C>
-void rec_subst(Ctx& ctx, Rec& rec, const std::vector<int>& layers, int ncols) {
-    ensure_tuned<C>(ctx, layers, ncols);  // at record time, before any capture
-    const Batch* b = &get_batch<C>(ctx, layers, ncols);
+void rec_subst(Ctx& ctx, Rec& rec, const std::vector<int>& layers, int ncols, bool approx = false) {
+    const int split = approx ? ctx.precond_split : 3;
+    ensure_tuned<C>(ctx, layers, ncols, split);  // at record time, before any capture
+    const Batch* b = &get_batch<C>(ctx, layers, ncols, split);
     Ctx* cp = &ctx;
     rec.add([cp, b, ncols](cudaStream_t st) { substitute<C>(*cp, *b, ncols, st); });
 }
@@ -669,7 +672,7 @@ void rec_apply_precond(Ctx& ctx, Rec& rec, const double2* x, int R, double2* y, 
         std::vector<int> one{j};
         rec_zero_slots<C>(ctx, rec, one, ldc);
         rec_inject<C>(ctx, rec, {make_inject<C>(ctx, j, true, pair_ptr(y, ctx, 0, j - 1), ntr, ldc, 0)}, R);
-        rec_subst<C>(ctx, rec, one, R);
+        rec_subst<C>(ctx, rec, one, R, true);
         rec_pairs_axpy(ctx, rec, pair_ptr(y, ctx, 0, j), ntr, pair_ptr(x, ctx, 0, j), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
         std::vector<Extract<C>> ex;
         for (int pl = 0; pl < 2; ++pl)
@@ -691,7 +694,7 @@ void rec_apply_precond(Ctx& ctx, Rec& rec, const double2* x, int R, double2* y, 
             if (l <= L - 2) inj.push_back(make_inject<C>(ctx, l, false, pair_ptr(y, ctx, 0, l), ntr, ldc, 0));
         }
         rec_inject<C>(ctx, rec, inj, R);
-        rec_subst<C>(ctx, rec, layers, R);
+        rec_subst<C>(ctx, rec, layers, R, true);
         std::vector<Extract<C>> ex;
         for (int j = 0; j < K; ++j)
             for (int pl = 0; pl < 2; ++pl)
@@ -704,7 +707,7 @@ void rec_apply_precond(Ctx& ctx, Rec& rec, const double2* x, int R, double2* y, 
         std::vector<int> one{j + 1};
         rec_zero_slots<C>(ctx, rec, one, ldc);
         rec_inject<C>(ctx, rec, {make_inject<C>(ctx, j + 1, false, pair_ptr(y, ctx, 1, j + 1), ntr, ldc, 0)}, R);
-        rec_subst<C>(ctx, rec, one, R);
+        rec_subst<C>(ctx, rec, one, R, true);
         rec_pairs_axpy(ctx, rec, pair_ptr(y, ctx, 1, j), ntr, pair_ptr(s, ctx, 1, j), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
         std::vector<Extract<C>> ex;
         for (int pl = 0; pl < 2; ++pl)

@@ -436,32 +436,33 @@ void substitute(Ctx& ctx, const Batch& b, int ncols, cudaStream_t st) {
     }
 }
 
-// Tensor-core eligibility of one node product: enough output and reduction tiles to fill a
-// 128-row block for more than one stage.
+// Tensor-core eligibility of one node product: at least min_tiles output tiles and a reduction
+// over at least two tiles (of any length when min_tiles <= 2, the autotuner's candidate that
+// puts almost every product on the tensor cores).
 static bool tc_node(int mode, const Node& nd, int min_tiles) {
     const int out_t = mode == 1 ? nd.upd_t : nd.own_t;
     const int red_t = mode == 2 ? nd.upd_t : nd.own_t;
-    return out_t >= min_tiles && red_t >= 2;
+    return out_t >= min_tiles && red_t >= (min_tiles <= 2 ? 1 : 2);
 }
 
-static std::string tune_key(const Ctx& ctx, const std::vector<int>& layers, int ldc) {
+static std::string tune_key(const Ctx& ctx, const std::vector<int>& layers, int ldc, int split) {
     std::vector<int> shapes;
     for (int l : layers) shapes.push_back(ctx.layers[l].shape);
     std::sort(shapes.begin(), shapes.end());
-    std::string key = "n" + std::to_string(ldc) + ":";
+    std::string key = "n" + std::to_string(ldc) + (split == 1 ? "s1" : "") + ":";
     for (int s : shapes) key += std::to_string(s) + ",";
     return key;
 }
 
 template <class C>
-Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols) {
+Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols, int split) {
     const bool dbl = sizeof(C) == 16;
     const int ldc = padded_ldc(dbl, ncols);
     const bool tc_ok = !dbl && tc_columns(ldc) > 0;
-    auto it = ctx.tuned.find(tune_key(ctx, layers, ldc));
+    auto it = ctx.tuned.find(tune_key(ctx, layers, ldc, split));
     if (it != ctx.tuned.end()) {
         const auto& ch = it->second;
-        return get_batch_cfg<C>(ctx, layers, ncols, ch.KS, ch.CC, tc_ok && ch.tc, ch.KS_tc);
+        return get_batch_cfg<C>(ctx, layers, ncols, ch.KS, ch.CC, tc_ok && ch.tc, ch.KS_tc, ch.min_t, split);
     }
     // default: split the reductions when the batch alone cannot fill the GPU
     const int nchunks = ldc / chunk_cols(dbl, ncols);
@@ -469,15 +470,15 @@ Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols) {
     const bool tc = tc_ok && ctx.tc_mode == 1;
     const int nchunks_tc = tc ? ldc / tc_columns(ldc) : 1;
     const int KS_tc = ((long long)layers.size() * nchunks_tc >= 32) ? (1 << 30) : ctx.tc_ks;
-    return get_batch_cfg<C>(ctx, layers, ncols, KS, 0, tc, KS_tc);
+    return get_batch_cfg<C>(ctx, layers, ncols, KS, 0, tc, KS_tc, ctx.tc_min_tiles, split);
 }
 
 template <class C>
-void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols) {
+void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols, int split) {
     const bool dbl = sizeof(C) == 16;
     const int ldc = padded_ldc(dbl, ncols);
     const bool tc_ok = !dbl && tc_columns(ldc) > 0;
-    const std::string key = tune_key(ctx, layers, ldc);
+    const std::string key = tune_key(ctx, layers, ldc, split);
     if (!ctx.autotune || ctx.tuned.count(key)) return;
     const int cc0 = chunk_cols(dbl, ncols);
     std::vector<Ctx::TuneChoice> cands;
@@ -485,10 +486,11 @@ void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols) {
         std::vector<int> ccs{cc0};
         if (cc0 >= 16 && ldc % (cc0 / 2) == 0) ccs.push_back(cc0 / 2);
         for (int cc : ccs)
-            for (int ks : {4, 8, 16, 1 << 30}) cands.push_back({ks, cc, 0, 1 << 30});
+            for (int ks : {4, 8, 16, 1 << 30}) cands.push_back({ks, cc, 0, 1 << 30, 0});
     }
     if (tc_ok && ctx.tc_mode >= 1)
-        for (int kstc : {4, 16, 1 << 30}) cands.push_back({8, cc0, 1, kstc});
+        for (int mt : {2, 4, ctx.tc_min_tiles})
+            for (int kstc : {16, 1 << 30}) cands.push_back({8, cc0, 1, kstc, mt});
     cudaEvent_t e0, e1;
     HZ_CUDA(cudaEventCreate(&e0));
     HZ_CUDA(cudaEventCreate(&e1));
@@ -498,7 +500,7 @@ void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols) {
     ctx.prof = false;
     std::string log = key + " ->";
     for (const auto& cd : cands) {
-        Batch& b = get_batch_cfg<C>(ctx, layers, ncols, cd.KS, cd.CC, cd.tc != 0, cd.KS_tc);
+        Batch& b = get_batch_cfg<C>(ctx, layers, ncols, cd.KS, cd.CC, cd.tc != 0, cd.KS_tc, cd.min_t, split);
         for (size_t j = 0; j < b.vec_ptrs.size(); ++j)
             HZ_CUDA(cudaMemsetAsync(b.vec_ptrs[j].first, 0, (size_t)b.vec_rows[j] * ldc * sizeof(C), ctx.stream));
         substitute<C>(ctx, b, ncols, ctx.stream);  // warm-up
@@ -508,8 +510,10 @@ void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols) {
         HZ_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
         HZ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        log += std::string(cd.tc ? " (TC, KS " : " (KS ") + std::to_string((cd.tc ? cd.KS_tc : cd.KS) > 1000 ? 0 : (cd.tc ? cd.KS_tc : cd.KS)) +
-               ", CC " + std::to_string(cd.CC) + ") " + std::to_string(ms) + " ms;";
+        const int ks_shown = cd.tc ? cd.KS_tc : cd.KS;
+        log += std::string(cd.tc ? " (TC, KS " : " (KS ") + std::to_string(ks_shown > 1000 ? 0 : ks_shown) +
+               ", CC " + std::to_string(cd.CC) + (cd.tc ? ", min " + std::to_string(cd.min_t) : std::string()) + ") " +
+               std::to_string(ms) + " ms;";
         if (ms < best) { best = ms; choice = cd; }
     }
     ctx.prof = prof;
@@ -520,11 +524,13 @@ void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols) {
 }
 
 template <class C>
-Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS, int CC, bool tc, int KS_tc) {
+Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS, int CC, bool tc, int KS_tc,
+                     int min_t, int split) {
     const bool dbl = sizeof(C) == 16;
     const int ldc = padded_ldc(dbl, ncols);
     std::string key = "KS" + std::to_string(KS) + "C" + std::to_string(CC) + "n" + std::to_string(ldc) +
-                      (tc ? "tc" + std::to_string(KS_tc) : "") + ":";
+                      (tc ? "tc" + std::to_string(KS_tc) + "m" + std::to_string(min_t) + "s" + std::to_string(split)
+                          : "") + ":";
     for (int l : layers) key += std::to_string(l) + ",";
     auto it = ctx.batches.find(key);
     if (it != ctx.batches.end()) return it->second;
@@ -534,6 +540,8 @@ Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS
     b.CC = CC;
     b.tc = tc;
     b.KS_tc = KS_tc;
+    b.min_t = min_t;
+    b.split = split;
     int H = 0;
     for (int l : layers) H = std::max(H, (int)ctx.shapes[ctx.layers[l].shape].levels.size());
     b.H = H;
@@ -545,7 +553,7 @@ Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS
             b.lvl_bytes[k][mode].assign(H, 0.0);
             b.lvl_flops[k][mode].assign(H, 0.0);
         }
-    auto split = [&](std::vector<Task>& out, int j, int nid, int tile, int k0, int k1, int ks) {
+    auto add_tasks = [&](std::vector<Task>& out, int j, int nid, int tile, int k0, int k1, int ks) {
         if (k1 <= k0) { out.push_back(Task{j, nid, tile, k0}); return; }
         for (int k = k0; k < k1; k += ks) out.push_back(Task{j, nid, tile, k});
     };
@@ -556,7 +564,7 @@ Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS
                 const Node& nd = sh.nodes[nid];
                 for (int mode = 0; mode < 4; ++mode) {
                     const int out_t = mode == 1 ? nd.upd_t : nd.own_t;
-                    const bool on_tc = tc && tc_node(mode, nd, ctx.tc_min_tiles);
+                    const bool on_tc = tc && tc_node(mode, nd, b.min_t);
                     // stored factor entries this product reads (triangular L^{-1} or L21)
                     const double ent = (mode == FA || mode == BB) ? (double)nd.nown * (nd.nown + 1) / 2.0
                                                                   : (double)nd.nown * nd.nupd;
@@ -564,17 +572,17 @@ Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS
                     b.lvl_flops[on_tc][mode][h] += 8.0 * ent;
                     if (on_tc) {
                         for (int t = 0; t < out_t; t += 4) {
-                            if (mode == 0) split(quads[0][h], j, nid, t, 0, std::min(t + 4, nd.own_t), b.KS_tc);
-                            if (mode == 1) split(quads[1][h], j, nid, t, 0, nd.own_t, b.KS_tc);
-                            if (mode == 2) split(quads[2][h], j, nid, t, 0, nd.upd_t, b.KS_tc);
-                            if (mode == 3) split(quads[3][h], j, nid, t, t, nd.own_t, b.KS_tc);
+                            if (mode == 0) add_tasks(quads[0][h], j, nid, t, 0, std::min(t + 4, nd.own_t), b.KS_tc);
+                            if (mode == 1) add_tasks(quads[1][h], j, nid, t, 0, nd.own_t, b.KS_tc);
+                            if (mode == 2) add_tasks(quads[2][h], j, nid, t, 0, nd.upd_t, b.KS_tc);
+                            if (mode == 3) add_tasks(quads[3][h], j, nid, t, t, nd.own_t, b.KS_tc);
                         }
                     } else {
                         for (int t = 0; t < out_t; ++t) {
-                            if (mode == 0) split(lists[0][h], j, nid, t, 0, t + 1, KS);      // FA: Linv row tile t
-                            if (mode == 1) split(lists[1][h], j, nid, t, 0, nd.own_t, KS);   // FB: L21 row tile t
-                            if (mode == 2) split(lists[2][h], j, nid, t, 0, nd.upd_t, KS);   // BA (>= 1 task)
-                            if (mode == 3) split(lists[3][h], j, nid, t, t, nd.own_t, KS);   // BB
+                            if (mode == 0) add_tasks(lists[0][h], j, nid, t, 0, t + 1, KS);      // FA: Linv row tile t
+                            if (mode == 1) add_tasks(lists[1][h], j, nid, t, 0, nd.own_t, KS);   // FB: L21 row tile t
+                            if (mode == 2) add_tasks(lists[2][h], j, nid, t, 0, nd.upd_t, KS);   // BA (>= 1 task)
+                            if (mode == 3) add_tasks(lists[3][h], j, nid, t, t, nd.own_t, KS);   // BB
                         }
                     }
                 }
@@ -638,11 +646,11 @@ void free_batches(Ctx& ctx) {
 
 template void substitute<float2>(Ctx&, const Batch&, int, cudaStream_t);
 template void substitute<double2>(Ctx&, const Batch&, int, cudaStream_t);
-template Batch& get_batch<float2>(Ctx&, const std::vector<int>&, int);
-template Batch& get_batch<double2>(Ctx&, const std::vector<int>&, int);
-template Batch& get_batch_cfg<float2>(Ctx&, const std::vector<int>&, int, int, int, bool, int);
-template Batch& get_batch_cfg<double2>(Ctx&, const std::vector<int>&, int, int, int, bool, int);
-template void ensure_tuned<float2>(Ctx&, const std::vector<int>&, int);
-template void ensure_tuned<double2>(Ctx&, const std::vector<int>&, int);
+template Batch& get_batch<float2>(Ctx&, const std::vector<int>&, int, int);
+template Batch& get_batch<double2>(Ctx&, const std::vector<int>&, int, int);
+template Batch& get_batch_cfg<float2>(Ctx&, const std::vector<int>&, int, int, int, bool, int, int, int);
+template Batch& get_batch_cfg<double2>(Ctx&, const std::vector<int>&, int, int, int, bool, int, int, int);
+template void ensure_tuned<float2>(Ctx&, const std::vector<int>&, int, int);
+template void ensure_tuned<double2>(Ctx&, const std::vector<int>&, int, int);
 
 }  // namespace hz

@@ -11,7 +11,9 @@
 // in TF32 with a three-term split of both operands (a = a_hi + a_lo, x = x_hi + x_lo;
 // a x ~ a_hi x_hi + a_hi x_lo + a_lo x_hi) and FP32 accumulation, which keeps every product at
 // FP32-level accuracy (about 2^-21 relative): 12 MMAs (M = 128, N = NT, K = 8) per 8 complex
-// reduction indices.
+// reduction indices.  SPLIT = 1 keeps only a_hi x_hi (plain TF32, about 2^-11 relative; 4 MMAs);
+// it is an option (HZ_PRECOND_SPLIT=1) for the local solves inside the preconditioner, whose
+// accuracy changes how fast GMRES converges but not the solution it converges to.
 //
 // Warp-specialized pipeline (416 threads, 16 complex reduction indices per stage, two-deep
 // rings of raw and converted buffers, every hand-off an mbarrier):
@@ -113,7 +115,7 @@ __device__ inline void cp_async_arrive(uint64_t* b) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" :: "r"(smem_u32(b)) : "memory");
 }
 
-template <int NT, int MODE>
+template <int NT, int MODE, int SPLIT>
 __global__ void __launch_bounds__(NTHREADS, 1) k_subst_tc(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ jobs,
                                                           int ldc, int nchunks, int KS, int* flag) {
     using LY = Layout<NT>;
@@ -236,16 +238,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_subst_tc(const Task* __restrict
                     re[0] = a0.x; im[0] = a0.y; re[1] = a0.z; im[1] = a0.w;
                     re[2] = a1.x; im[2] = a1.y; re[3] = a1.z; im[3] = a1.w;
                 }
-                float4 rh, rl, ih, il;
+                float4 rh, ih;
                 rh.x = tf32_hi(re[0]); rh.y = tf32_hi(re[1]); rh.z = tf32_hi(re[2]); rh.w = tf32_hi(re[3]);
                 ih.x = tf32_hi(im[0]); ih.y = tf32_hi(im[1]); ih.z = tf32_hi(im[2]); ih.w = tf32_hi(im[3]);
-                rl = make_float4(re[0] - rh.x, re[1] - rh.y, re[2] - rh.z, re[3] - rh.w);
-                il = make_float4(im[0] - ih.x, im[1] - ih.y, im[2] - ih.z, im[3] - ih.w);
                 const int off = coff(row, 4 * kq);
                 *(float4*)(cv + 0 * LY::A_MAT + off) = rh;
-                *(float4*)(cv + 1 * LY::A_MAT + off) = rl;
                 *(float4*)(cv + 2 * LY::A_MAT + off) = ih;
-                *(float4*)(cv + 3 * LY::A_MAT + off) = il;
+                if (SPLIT == 3) {
+                    *(float4*)(cv + 1 * LY::A_MAT + off) = make_float4(re[0] - rh.x, re[1] - rh.y, re[2] - rh.z, re[3] - rh.w);
+                    *(float4*)(cv + 3 * LY::A_MAT + off) = make_float4(im[0] - ih.x, im[1] - ih.y, im[2] - ih.z, im[3] - ih.w);
+                }
             }
             for (int id = ct; id < NT * 4; id += NCONVT) {   // vector operand: NT rows x 16 k
                 const int n = id % NT, kq = id / NT;
@@ -253,16 +255,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_subst_tc(const Task* __restrict
                 float re[4], im[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) { float2 a = src[(4 * kq + j) * NT + n]; re[j] = a.x; im[j] = a.y; }
-                float4 rh, rl, ih, il;
+                float4 rh, ih;
                 rh.x = tf32_hi(re[0]); rh.y = tf32_hi(re[1]); rh.z = tf32_hi(re[2]); rh.w = tf32_hi(re[3]);
                 ih.x = tf32_hi(im[0]); ih.y = tf32_hi(im[1]); ih.z = tf32_hi(im[2]); ih.w = tf32_hi(im[3]);
-                rl = make_float4(re[0] - rh.x, re[1] - rh.y, re[2] - rh.z, re[3] - rh.w);
-                il = make_float4(im[0] - ih.x, im[1] - ih.y, im[2] - ih.z, im[3] - ih.w);
                 const int off = 4 * LY::A_MAT + coff(n, 4 * kq);
                 *(float4*)(cv + off + 0 * LY::X_MAT) = rh;
-                *(float4*)(cv + off + 1 * LY::X_MAT) = rl;
                 *(float4*)(cv + off + 2 * LY::X_MAT) = ih;
-                *(float4*)(cv + off + 3 * LY::X_MAT) = il;
+                if (SPLIT == 3) {
+                    *(float4*)(cv + off + 1 * LY::X_MAT) = make_float4(re[0] - rh.x, re[1] - rh.y, re[2] - rh.z, re[3] - rh.w);
+                    *(float4*)(cv + off + 3 * LY::X_MAT) = make_float4(im[0] - ih.x, im[1] - ih.y, im[2] - ih.z, im[3] - ih.w);
+                }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(raw_empty + slot);
@@ -288,17 +290,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_subst_tc(const Task* __restrict
                 const uint64_t xih = smem_desc(xb + 2 * LY::X_MAT), xil = smem_desc(xb + 3 * LY::X_MAT);
                 const uint32_t first = (s == 0 && ks == 0) ? 0u : 1u;
                 mma_tf32(tm_r, arh, xrh, idesc, first);      // Yr = Ar Xr - Ai Xi
-                mma_tf32(tm_r, arh, xrl, idesc, 1u);
-                mma_tf32(tm_r, arl, xrh, idesc, 1u);
                 mma_tf32(tm_r, aih, xih, idesc_neg, 1u);
-                mma_tf32(tm_r, aih, xil, idesc_neg, 1u);
-                mma_tf32(tm_r, ail, xih, idesc_neg, 1u);
                 mma_tf32(tm_i, aih, xrh, idesc, first);      // Yi = Ai Xr + Ar Xi
-                mma_tf32(tm_i, aih, xrl, idesc, 1u);
-                mma_tf32(tm_i, ail, xrh, idesc, 1u);
                 mma_tf32(tm_i, arh, xih, idesc, 1u);
-                mma_tf32(tm_i, arh, xil, idesc, 1u);
-                mma_tf32(tm_i, arl, xih, idesc, 1u);
+                if (SPLIT == 3) {                             // hi x lo and lo x hi terms
+                    mma_tf32(tm_r, arh, xrl, idesc, 1u);
+                    mma_tf32(tm_r, arl, xrh, idesc, 1u);
+                    mma_tf32(tm_r, aih, xil, idesc_neg, 1u);
+                    mma_tf32(tm_r, ail, xih, idesc_neg, 1u);
+                    mma_tf32(tm_i, aih, xrl, idesc, 1u);
+                    mma_tf32(tm_i, ail, xrh, idesc, 1u);
+                    mma_tf32(tm_i, arh, xil, idesc, 1u);
+                    mma_tf32(tm_i, arl, xih, idesc, 1u);
+                }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(smem_u32(conv_empty + cb)));
@@ -415,29 +419,31 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_subst_tc(const Task* __restrict
     if (w == mma_warp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(2 * NT));
 }
 
-template <int NT, int MODE>
+template <int NT, int MODE, int SPLIT>
 void launch_one(const Task* tasks, long long n, const JobDev<float2>* jobs, int ldc, int KS, int* flag, cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
-        HZ_CUDA(cudaFuncSetAttribute(k_subst_tc<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, Layout<NT>::TOTAL));
+        HZ_CUDA(cudaFuncSetAttribute(k_subst_tc<NT, MODE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     Layout<NT>::TOTAL));
         attr = true;
     }
     const int nchunks = ldc / NT;
-    k_subst_tc<NT, MODE><<<(unsigned)(n * nchunks), NTHREADS, Layout<NT>::TOTAL, st>>>(tasks, jobs, ldc, nchunks, KS, flag);
+    k_subst_tc<NT, MODE, SPLIT><<<(unsigned)(n * nchunks), NTHREADS, Layout<NT>::TOTAL, st>>>(tasks, jobs, ldc, nchunks,
+                                                                                               KS, flag);
     HZ_CHECK_LAUNCH();
 }
 
-template <int NT>
+template <int NT, int SPLIT>
 void launch_mode(const Batch& b, int h, int mode, int ldc, int* flag, cudaStream_t st) {
     const long long off = b.pair_off[mode][h], n = b.pair_cnt[mode][h];
     if (n == 0) return;
     const Task* tasks = b.d_tasks + off;
     const JobDev<float2>* jobs = (const JobDev<float2>*)b.d_jobs;
     switch (mode) {
-        case FA: launch_one<NT, FA>(tasks, n, jobs, ldc, b.KS_tc, flag, st); break;
-        case FB: launch_one<NT, FB>(tasks, n, jobs, ldc, b.KS_tc, flag, st); break;
-        case BA: launch_one<NT, BA>(tasks, n, jobs, ldc, b.KS_tc, flag, st); break;
-        default: launch_one<NT, BB>(tasks, n, jobs, ldc, b.KS_tc, flag, st); break;
+        case FA: launch_one<NT, FA, SPLIT>(tasks, n, jobs, ldc, b.KS_tc, flag, st); break;
+        case FB: launch_one<NT, FB, SPLIT>(tasks, n, jobs, ldc, b.KS_tc, flag, st); break;
+        case BA: launch_one<NT, BA, SPLIT>(tasks, n, jobs, ldc, b.KS_tc, flag, st); break;
+        default: launch_one<NT, BB, SPLIT>(tasks, n, jobs, ldc, b.KS_tc, flag, st); break;
     }
 }
 
@@ -450,8 +456,14 @@ int tc_columns(int ldc) {
 }
 
 void launch_level_tc(const Batch& b, int h, int mode, int ldc, int* flag, cudaStream_t st) {
-    if (tc_columns(ldc) == 128) launch_mode<128>(b, h, mode, ldc, flag, st);
-    else launch_mode<64>(b, h, mode, ldc, flag, st);
+    const bool wide = tc_columns(ldc) == 128;
+    if (b.split == 1) {
+        if (wide) launch_mode<128, 1>(b, h, mode, ldc, flag, st);
+        else launch_mode<64, 1>(b, h, mode, ldc, flag, st);
+    } else {
+        if (wide) launch_mode<128, 3>(b, h, mode, ldc, flag, st);
+        else launch_mode<64, 3>(b, h, mode, ldc, flag, st);
+    }
 }
 
 }  // namespace hz

@@ -277,6 +277,54 @@ def test_tensor_core_and_cuda_core_paths_agree(hz, monkeypatch):
     assert rel(outs[2], outs[1]) < 1e-8
 
 
+@pytest.mark.parametrize("split", ["3", "1"])
+def test_tensor_core_preconditioner_precision(hz, small_case, split, monkeypatch):
+    """P on 64 trace columns with the tensor-core path: with three-term TF32 products it matches
+    the oracle's P within the mixed stage tolerance; with single-term TF32 products (the option
+    HZ_PRECOND_SPLIT=1) within 5e-3, while M_pol keeps the three-term accuracy."""
+    monkeypatch.setenv("HZ_SUBST_TC", "1")
+    monkeypatch.setenv("HZ_TC_MIN_TILES", "2")
+    monkeypatch.setenv("HZ_PRECOND_SPLIT", split)
+    p, M = small_case
+    s = make_solver(hz, p, "mixed")
+    R = 64
+    rng = np.random.default_rng(77)
+    shp = s.trace_shape(R)
+    x = rng.standard_normal(shp) + 1j * rng.standard_normal(shp)
+    z = s.apply_precond(cuda(x)).cpu().numpy()
+    y = s.apply_mpol(cuda(x)).cpu().numpy()
+    tol = STAGE_TOL["mixed"] if split == "3" else 5e-3
+    for r in (0, 33, 63):
+        zd, zu = M.apply_P(x[r, 0], x[r, 1])
+        assert rel(z[r, 0], zd) < tol and rel(z[r, 1], zu) < tol, (r, rel(z[r, 0], zd), rel(z[r, 1], zu))
+        yd, yu = M.apply_Mpol(x[r, 0], x[r, 1])
+        assert rel(y[r, 0], yd) < STAGE_TOL["mixed"] and rel(y[r, 1], yu) < STAGE_TOL["mixed"]
+    s.close()
+
+
+def test_fast_preconditioner_solution_unchanged(hz, monkeypatch):
+    """The solution does not depend on the precision of the preconditioner's tensor-core
+    products (they only steer GMRES): single- and three-term runs agree after the FP64 residual
+    check, and both meet the oracle's solution."""
+    monkeypatch.setenv("HZ_SUBST_TC", "1")
+    monkeypatch.setenv("HZ_TC_MIN_TILES", "2")
+    p = W.small_problem(24, 4, 4, seed=41, R=64)
+    f = p.rhs()
+    outs, iters = [], []
+    for split in ("3", "1"):
+        monkeypatch.setenv("HZ_PRECOND_SPLIT", split)
+        s = make_solver(hz, p, "mixed")
+        u, info, _ = s.solve(cuda(f))
+        outs.append(u.cpu().numpy())
+        iters.append(info[0].iters)
+        assert all(i.volume_relres < 1e-8 for i in info)
+        s.close()
+    assert rel(outs[0], outs[1]) < 1e-7
+    ref = direct.solve(p.m, p.omega, p.npml, p.C, f[:2])
+    assert rel(outs[1][:2], ref) < E2E_TOL["mixed"]
+    assert iters[1] <= iters[0] + 2, iters
+
+
 def test_profile_detail_attributes_launches_by_kernel_kind(hz, small_case, monkeypatch):
     """Detail profiling times every substitution launch and attributes it to the CUDA-core or
     the tensor-core kernel; the algorithmic flops of the two kinds add up to those of the
