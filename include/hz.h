@@ -107,6 +107,8 @@ void hz_default_opts(hz_precision prec, hz_solve_opts* opts);
  *   HZ_TC_MIN_TILES   default minimum output tiles of a tensor-core product (8)
  *   HZ_PRECOND_SPLIT  1: single-term TF32 tensor-core products inside the preconditioner
  *                     (default 3 terms, FP32-level)
+ *   HZ_TC_CFG=1       with HZ_AUTOTUNE=0: the persistent tensor-core kernel (one block per SM
+ *                     walking the work items) instead of one block per work item (0)
  *   HZ_AUTOTUNE=0     keep the fixed defaults; HZ_GRAPHS=0 no CUDA-graph replay;
  *   HZ_LEAF           nested-dissection leaf size (cells, default 64)
  */

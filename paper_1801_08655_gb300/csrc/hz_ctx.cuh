@@ -37,6 +37,7 @@ struct Batch {
     int KS_tc = 1 << 30;                        // split-K of the tensor-core tasks (tiles)
     int min_t = 8;                              // output tiles a node product needs for the tensor cores
     int split = 3;                              // TF32 terms per real product on the tensor cores (3 or 1)
+    int tc_cfg = 0;                             // tensor-core kernel: 0 one block per work item, 1 persistent
     std::vector<long long> pair_off[4], pair_cnt[4];  // tensor-core tasks: two output tiles each
     Task* d_tasks = nullptr;
     void* d_jobs = nullptr;                     // JobDev<C>[njobs]
@@ -171,13 +172,14 @@ struct Ctx {
     std::map<long long, std::unique_ptr<Rec>> plans;   // matvec plans by column count
     // autotuner: (shape signature, ldc) -> chosen split-K depth and column chunk
     bool autotune = true;
-    struct TuneChoice { int KS, CC, tc, KS_tc, min_t; };
+    struct TuneChoice { int KS, CC, tc, KS_tc, min_t, tc_cfg; };
     std::map<std::string, TuneChoice> tuned;
     std::vector<std::string> tune_log;
     int tc_mode = 2;        // tensor-core substitution (complex64, >= 64 columns): 0 never, 1 always,
                             // 2 when the autotuner measures it faster for the batch signature
     int tc_ks = 4;          // split-K (factor tiles per block) of small tensor-core batches
     int tc_min_tiles = 8;   // output tiles a node product needs to run on the tensor cores
+    int tc_cfg = 0;         // untuned tensor-core kernel: 0 one block per work item, 1 persistent (HZ_TC_CFG)
     int precond_split = 3;  // TF32 terms of the tensor-core products inside the preconditioner (3 or 1)
     std::vector<ProfRec> prof_recs;
     bool prof_detail = false;                 // also time every substitution launch by kernel kind

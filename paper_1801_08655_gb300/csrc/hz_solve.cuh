@@ -15,7 +15,7 @@ int padded_ldc(bool is_double, int ncols);
 template <class C> Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols, int split = 3);
 // Build (or fetch) a batch with an explicit split-K depth and column chunk.
 template <class C> Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS, int CC, bool tc,
-                                       int KS_tc, int min_t, int split = 3);
+                                       int KS_tc, int min_t, int split = 3, int tc_cfg = 0);
 // Autotune the substitution of this batch signature (times candidate split-K depths and column
 // chunks on zeroed slot vectors); a no-op once the signature is tuned or when tuning is off.
 template <class C> void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols, int split = 3);

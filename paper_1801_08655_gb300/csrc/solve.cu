@@ -462,7 +462,7 @@ Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols, int split)
     auto it = ctx.tuned.find(tune_key(ctx, layers, ldc, split));
     if (it != ctx.tuned.end()) {
         const auto& ch = it->second;
-        return get_batch_cfg<C>(ctx, layers, ncols, ch.KS, ch.CC, tc_ok && ch.tc, ch.KS_tc, ch.min_t, split);
+        return get_batch_cfg<C>(ctx, layers, ncols, ch.KS, ch.CC, tc_ok && ch.tc, ch.KS_tc, ch.min_t, split, ch.tc_cfg);
     }
     // default: split the reductions when the batch alone cannot fill the GPU
     const int nchunks = ldc / chunk_cols(dbl, ncols);
@@ -470,7 +470,7 @@ Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols, int split)
     const bool tc = tc_ok && ctx.tc_mode == 1;
     const int nchunks_tc = tc ? ldc / tc_columns(ldc) : 1;
     const int KS_tc = ((long long)layers.size() * nchunks_tc >= 32) ? (1 << 30) : ctx.tc_ks;
-    return get_batch_cfg<C>(ctx, layers, ncols, KS, 0, tc, KS_tc, ctx.tc_min_tiles, split);
+    return get_batch_cfg<C>(ctx, layers, ncols, KS, 0, tc, KS_tc, ctx.tc_min_tiles, split, ctx.tc_cfg);
 }
 
 template <class C>
@@ -482,15 +482,19 @@ void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols, int split
     if (!ctx.autotune || ctx.tuned.count(key)) return;
     const int cc0 = chunk_cols(dbl, ncols);
     std::vector<Ctx::TuneChoice> cands;
+    const bool try_tc = tc_ok && ctx.tc_mode >= 1;
     if (ctx.tc_mode != 1 || !tc_ok) {
+        // CUDA-core candidates (fewer when the tensor-core kernel competes for these columns)
         std::vector<int> ccs{cc0};
-        if (cc0 >= 16 && ldc % (cc0 / 2) == 0) ccs.push_back(cc0 / 2);
+        if (!try_tc && cc0 >= 16 && ldc % (cc0 / 2) == 0) ccs.push_back(cc0 / 2);
         for (int cc : ccs)
-            for (int ks : {4, 8, 16, 1 << 30}) cands.push_back({ks, cc, 0, 1 << 30, 0});
+            for (int ks : {4, 8, 16, 1 << 30})
+                if (!try_tc || ks == 8 || ks == (1 << 30)) cands.push_back({ks, cc, 0, 1 << 30, 0, 0});
     }
-    if (tc_ok && ctx.tc_mode >= 1)
-        for (int mt : {2, 4, ctx.tc_min_tiles})
-            for (int kstc : {16, 1 << 30}) cands.push_back({8, cc0, 1, kstc, mt});
+    if (try_tc)
+        for (int cfg : {1, 0})   // persistent / one block per work item
+            for (int mt : {2, 4, ctx.tc_min_tiles})
+                for (int kstc : {16, 1 << 30}) cands.push_back({8, cc0, 1, kstc, mt, cfg});
     cudaEvent_t e0, e1;
     HZ_CUDA(cudaEventCreate(&e0));
     HZ_CUDA(cudaEventCreate(&e1));
@@ -500,7 +504,7 @@ void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols, int split
     ctx.prof = false;
     std::string log = key + " ->";
     for (const auto& cd : cands) {
-        Batch& b = get_batch_cfg<C>(ctx, layers, ncols, cd.KS, cd.CC, cd.tc != 0, cd.KS_tc, cd.min_t, split);
+        Batch& b = get_batch_cfg<C>(ctx, layers, ncols, cd.KS, cd.CC, cd.tc != 0, cd.KS_tc, cd.min_t, split, cd.tc_cfg);
         for (size_t j = 0; j < b.vec_ptrs.size(); ++j)
             HZ_CUDA(cudaMemsetAsync(b.vec_ptrs[j].first, 0, (size_t)b.vec_rows[j] * ldc * sizeof(C), ctx.stream));
         substitute<C>(ctx, b, ncols, ctx.stream);  // warm-up
@@ -512,7 +516,8 @@ void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols, int split
         HZ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         const int ks_shown = cd.tc ? cd.KS_tc : cd.KS;
         log += std::string(cd.tc ? " (TC, KS " : " (KS ") + std::to_string(ks_shown > 1000 ? 0 : ks_shown) +
-               ", CC " + std::to_string(cd.CC) + (cd.tc ? ", min " + std::to_string(cd.min_t) : std::string()) + ") " +
+               ", CC " + std::to_string(cd.CC) +
+               (cd.tc ? ", min " + std::to_string(cd.min_t) + ", cfg " + std::to_string(cd.tc_cfg) : std::string()) + ") " +
                std::to_string(ms) + " ms;";
         if (ms < best) { best = ms; choice = cd; }
     }
@@ -525,11 +530,12 @@ void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols, int split
 
 template <class C>
 Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS, int CC, bool tc, int KS_tc,
-                     int min_t, int split) {
+                     int min_t, int split, int tc_cfg) {
     const bool dbl = sizeof(C) == 16;
     const int ldc = padded_ldc(dbl, ncols);
     std::string key = "KS" + std::to_string(KS) + "C" + std::to_string(CC) + "n" + std::to_string(ldc) +
-                      (tc ? "tc" + std::to_string(KS_tc) + "m" + std::to_string(min_t) + "s" + std::to_string(split)
+                      (tc ? "tc" + std::to_string(KS_tc) + "m" + std::to_string(min_t) + "s" + std::to_string(split) +
+                                "c" + std::to_string(tc_cfg)
                           : "") + ":";
     for (int l : layers) key += std::to_string(l) + ",";
     auto it = ctx.batches.find(key);
@@ -542,6 +548,7 @@ Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS
     b.KS_tc = KS_tc;
     b.min_t = min_t;
     b.split = split;
+    b.tc_cfg = tc_cfg;
     int H = 0;
     for (int l : layers) H = std::max(H, (int)ctx.shapes[ctx.layers[l].shape].levels.size());
     b.H = H;
@@ -588,6 +595,18 @@ Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS
                 }
             }
     }
+    // tensor-core work items longest reduction first: the persistent kernel deals them out
+    // round-robin, and either kernel then ends a launch on short items
+    for (int mode = 0; mode < 4; ++mode)
+        for (int h = 0; h < H; ++h) {
+            auto red_len = [&](const Task& tk) {
+                const Node& nd = ctx.shapes[ctx.layers[layers[tk.job]].shape].nodes[tk.node];
+                const int kend = mode == 0 ? std::min(tk.tile + 4, nd.own_t) : (mode == 2 ? nd.upd_t : nd.own_t);
+                return std::min(kend, tk.pad_ + std::min(b.KS_tc, 1 << 28)) - tk.pad_;
+            };
+            std::stable_sort(quads[mode][h].begin(), quads[mode][h].end(),
+                             [&](const Task& x, const Task& y) { return red_len(x) > red_len(y); });
+        }
     std::vector<Task> all;
     for (int mode = 0; mode < 4; ++mode) {
         b.pair_off[mode].assign(H, 0);
@@ -648,8 +667,8 @@ template void substitute<float2>(Ctx&, const Batch&, int, cudaStream_t);
 template void substitute<double2>(Ctx&, const Batch&, int, cudaStream_t);
 template Batch& get_batch<float2>(Ctx&, const std::vector<int>&, int, int);
 template Batch& get_batch<double2>(Ctx&, const std::vector<int>&, int, int);
-template Batch& get_batch_cfg<float2>(Ctx&, const std::vector<int>&, int, int, int, bool, int, int, int);
-template Batch& get_batch_cfg<double2>(Ctx&, const std::vector<int>&, int, int, int, bool, int, int, int);
+template Batch& get_batch_cfg<float2>(Ctx&, const std::vector<int>&, int, int, int, bool, int, int, int, int);
+template Batch& get_batch_cfg<double2>(Ctx&, const std::vector<int>&, int, int, int, bool, int, int, int, int);
 template void ensure_tuned<float2>(Ctx&, const std::vector<int>&, int, int);
 template void ensure_tuned<double2>(Ctx&, const std::vector<int>&, int, int);
 

@@ -1,9 +1,9 @@
 // Tensor-core (tcgen05) variant of the substitution products for complex64 factors.
 //
-// A block computes 128 complex output rows (four factor tile rows) x NT right-hand-side
-// columns of one of the four node products of the substitution (see solve.cu), for the
-// nodes whose products are large enough to fill it; smaller nodes of the same tree level run
-// on the CUDA-core kernel in the same phase.
+// A work item computes 128 complex output rows (four factor tile rows) x NT right-hand-side
+// columns of one of the four node products of the substitution (see solve.cu), for the nodes
+// whose products are large enough to fill it; smaller nodes of the same tree level run on the
+// CUDA-core kernel in the same phase.
 //
 // The complex product Y = A X is four real products with two accumulators in tensor memory:
 //     Yr = Ar Xr - Ai Xi,    Yi = Ai Xr + Ar Xi,
@@ -15,20 +15,27 @@
 // it is an option (HZ_PRECOND_SPLIT=1) for the local solves inside the preconditioner, whose
 // accuracy changes how fast GMRES converges but not the solution it converges to.
 //
-// Warp-specialized pipeline (416 threads, 16 complex reduction indices per stage, two-deep
-// rings of raw and converted buffers, every hand-off an mbarrier):
+// Warp-specialized pipeline (16 complex reduction indices per stage, two-deep rings of raw and
+// converted buffers, every hand-off an mbarrier):
 //   4 loader warps    : cp.async 16-byte copies of the factor tiles and vector rows into a raw
 //                       buffer (masked rows / absent tiles zero-filled by the copy), completion
 //                       signalled with cp.async.mbarrier.arrive;
 //   8 converter warps : raw -> split hi/lo TF32 operands in the K-major core-matrix layout
 //                       (no swizzle), 16-byte stores;
-//   1 MMA warp        : one thread issues the 24 MMAs of a stage and commits them to the
-//                       mbarrier that releases the converted buffer.
-// The epilogue (converter warps) stages both accumulators from tensor memory (tcgen05.ld;
-// lane = complex row) through shared memory and writes whole rows with 16-byte accesses: a
-// task that covers the full reduction of its rows stores them, split reductions and the
-// shared update rows of FB accumulate with vector atomics.  Every mbarrier wait is bounded and
-// the outcome block-uniform; on timeout the block records an error flag, waits once more
+//   1 MMA warp        : one thread issues the MMAs of a stage and commits them to the mbarrier
+//                       that releases the converted buffer.
+// Two kernels share these stages:
+//   k_subst_tc  (one block per work item, 416 threads): after the last MMA the converter warps
+//               stage the accumulators through shared memory and write whole rows;
+//   k_subst_tcp (persistent, one block per SM, 544 threads): the block walks the launch's work
+//               items with stride gridDim.x; the rings run on across items, the accumulators
+//               alternate between two TMEM buffers, and 4 epilogue warps drain item i while the
+//               MMA warp accumulates item i+1, so block start-up, pipeline fill and epilogue are
+//               paid once per SM instead of once per item.
+// Output rule of both: an item that covers the full reduction of its rows stores them; split
+// reductions and the shared update rows of FB accumulate with vector atomics.  Every mbarrier
+// wait is bounded (polls and wall time); a wait that gives up raises an abort flag in shared
+// memory that ends the block's other waits; the block then records an error flag, waits
 // (bounded) for its own MMAs, frees its tensor memory and exits.
 #include <algorithm>
 
@@ -45,9 +52,11 @@ enum { FA = 0, FB = 1, BA = 2, BB = 3 };
 constexpr int KC = 16;                 // complex reduction indices per stage
 constexpr int LBO = 128;               // bytes between core matrices along K
 constexpr int SBO = (KC / 4) * 128;    // bytes between 8-row groups (K = 16 tf32 per row)
-constexpr int MR = 128;                // complex output rows per block (4 tiles)
+constexpr int MR = 128;                // complex output rows per work item (4 tiles)
 constexpr int TROW = KC * 8 + 16;      // padded raw row (transposed tiles): 144 bytes
-constexpr long long WAIT_LIMIT = 1LL << 26;
+constexpr long long WAIT_LIMIT = 1LL << 26;            // polls of one mbarrier wait at most ...
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // ... and at most 2 s of wall time
+constexpr int NLOAD = 128, NCONV = 256;                // loader and converter threads
 
 __device__ inline long long tri_idx(int rt, int ct) { return (long long)rt * (rt + 1) / 2 + ct; }
 
@@ -75,13 +84,29 @@ __device__ inline void cp16(uint32_t dst, const void* src, int src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 
-__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ inline unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the phase of the given parity: gives up (false) after WAIT_LIMIT polls,
+// WAIT_NS of wall time, or as soon as another role of the block has raised *abort.
+__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+    unsigned long long t0 = 0;
     for (long long it = 0; it < WAIT_LIMIT; ++it) {
         uint32_t ok;
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
                      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
         if (ok) return true;
+        if ((it & 255) == 255) {
+            if (*abort) return false;
+            const unsigned long long now = global_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > WAIT_NS) break;
+        }
     }
+    *abort = 1;
     return false;
 }
 
@@ -90,19 +115,6 @@ __device__ inline void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t ide
                  "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
                  :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
-
-template <int NT> struct Layout {
-    static constexpr int A_MAT = MR * KC * 4;            // one real operand matrix (8 KB)
-    static constexpr int X_MAT = NT * KC * 4;
-    static constexpr int CONV = 4 * A_MAT + 4 * X_MAT;   // Ar_h Ar_l Ai_h Ai_l  Xr_h Xr_l Xi_h Xi_l
-    static constexpr int RAW_A = 4 * 32 * TROW;          // large enough for both raw tile layouts
-    static constexpr int RAW_X = KC * NT * 8;
-    static constexpr int RAW = RAW_A + RAW_X;
-    static constexpr int TOTAL = 2 * CONV + 2 * RAW + 128;
-};
-
-// thread roles (warp-specialized): 4 loader warps, 8 converter warps, 1 MMA warp
-constexpr int NLOAD = 128, NCONVT = 256, NTHREADS = NLOAD + NCONVT + 32;
 
 __device__ inline void mbar_init(uint64_t* b, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(b)), "r"(count));
@@ -114,37 +126,258 @@ __device__ inline void mbar_arrive(uint64_t* b) {
 __device__ inline void cp_async_arrive(uint64_t* b) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" :: "r"(smem_u32(b)) : "memory");
 }
+__device__ inline void mma_commit(uint64_t* b) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(smem_u32(b)));
+}
+
+// 16 consecutive accumulator columns of this warp's 32 TMEM lanes (real and imaginary part)
+__device__ inline void tmem_ld16(uint32_t ar, uint32_t ai, uint32_t (&vr)[16], uint32_t (&vi)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]), "=r"(vr[7]),
+                   "=r"(vr[8]), "=r"(vr[9]), "=r"(vr[10]), "=r"(vr[11]), "=r"(vr[12]), "=r"(vr[13]), "=r"(vr[14]), "=r"(vr[15])
+                 : "r"(ar));
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]), "=r"(vi[7]),
+                   "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]), "=r"(vi[13]), "=r"(vi[14]), "=r"(vi[15])
+                 : "r"(ai));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Sizes of one ring stage for NT columns.
+template <int NT> struct Ring {
+    static constexpr int A_MAT = MR * KC * 4;            // one real operand matrix (8 KB)
+    static constexpr int X_MAT = NT * KC * 4;
+    static constexpr int CONV = 4 * A_MAT + 4 * X_MAT;   // Ar_h Ar_l Ai_h Ai_l  Xr_h Xr_l Xi_h Xi_l
+    static constexpr int RAW_A = 4 * 32 * TROW;          // large enough for both raw tile layouts
+    static constexpr int RAW_X = KC * NT * 8;
+    static constexpr int RAW = RAW_A + RAW_X;
+    static constexpr int BYTES = 2 * (CONV + RAW);       // two-deep rings
+};
+
+// One work item: 128 output rows (tiles o0 .. o0+3) x NT columns of one node product, reduction
+// tiles [kbeg, kend).
+struct Item {
+    JobDev<float2> jb;
+    NodeDev nd;
+    int col0, o0, nout_t, nrows_out, nrows_k, kbeg, kend, nst;
+    bool unique;
+};
+
+template <int NT, int MODE>
+__device__ inline Item decode(const Task* tasks, const JobDev<float2>* jobs, long long item, int nchunks, int KS) {
+    Item it;
+    const Task tk = tasks[item / nchunks];
+    it.jb = jobs[tk.job];
+    it.nd = it.jb.nodes[tk.node];
+    const NodeDev& nd = it.nd;
+    it.col0 = (int)(item % nchunks) * NT;
+    it.o0 = tk.tile;
+    it.nout_t = (MODE == FB) ? nd.upd_t : nd.own_t;
+    it.nrows_out = (MODE == FB) ? nd.nupd : nd.nown;
+    it.nrows_k = (MODE == BA) ? nd.nupd : nd.nown;
+    it.kbeg = tk.pad_;
+    const int kfull0 = (MODE == BB) ? it.o0 : 0;
+    const int kfull1 = (MODE == FA) ? min(it.o0 + 4, nd.own_t) : ((MODE == BA) ? nd.upd_t : nd.own_t);
+    it.kend = min(kfull1, it.kbeg + KS);
+    it.nst = max(0, it.kend - it.kbeg) * 2;
+    it.unique = it.kbeg == kfull0 && it.kend == kfull1 && MODE != FB;
+    return it;
+}
+
+// Loader part of stage s of an item: the four factor tiles' 16-column halves and 16 vector rows.
+template <int NT, int MODE>
+__device__ inline void load_stage(unsigned char* rb, const Item& it, int s, int ldc, int t) {
+    using RG = Ring<NT>;
+    constexpr bool TR = (MODE == BA || MODE == BB);  // factor tiles used transposed
+    const NodeDev& nd = it.nd;
+    const int kt = it.kbeg + (s >> 1), hk = s & 1;
+    for (int c = t; c < 1024; c += NLOAD) {     // factor tiles: 1024 chunks of 16 bytes
+        const int oi = c >> 8, q = c & 255;
+        const int o = it.o0 + oi;
+        bool exists = o < it.nout_t;
+        if (MODE == FA) exists = exists && kt <= o;
+        if (MODE == BB) exists = exists && kt >= o;
+        long long toff = 0;
+        if (exists) {
+            if (MODE == FA) toff = nd.linv_off + tri_idx(o, kt);
+            else if (MODE == FB) toff = nd.l21_off + (long long)o * nd.own_t + kt;
+            else if (MODE == BA) toff = nd.l21_off + (long long)kt * nd.own_t + o;
+            else toff = nd.linv_off + tri_idx(kt, o);
+        }
+        const float2* tl = it.jb.fac + toff * TILE2;
+        uint32_t dst;
+        const float2* src;
+        if (!TR) {
+            dst = smem_u32(rb + oi * 4096 + q * 16);
+            src = tl + hk * KC * 32 + q * 2;
+        } else {
+            const int r = q >> 3, j = q & 7;
+            dst = smem_u32(rb + oi * 32 * TROW + r * TROW + j * 16);
+            src = tl + 32 * r + hk * KC + j * 2;
+        }
+        cp16(dst, exists ? (const void*)src : (const void*)it.jb.fac, exists ? 16 : 0);
+    }
+    const float2* vec = (MODE == FA || MODE == BB) ? it.jb.acc : it.jb.x;
+    const int* upd = it.jb.upd_idx + nd.upd_off;
+    for (int c = t; c < KC * NT / 2; c += NLOAD) {  // vector rows: KC x NT, raw [k][n]
+        const int k = c / (NT / 2), j = c % (NT / 2);
+        const int rr = kt * TILE + hk * KC + k;
+        const bool v = rr < it.nrows_k;
+        long long row = 0;
+        if (v) row = (MODE == BA) ? (long long)upd[rr] : (long long)(nd.own0 + rr);
+        cp16(smem_u32(rb + RG::RAW_A + k * NT * 8 + j * 16), vec + row * ldc + it.col0 + 2 * j, v ? 16 : 0);
+    }
+}
+
+// Converter part of a stage: raw -> hi (and lo) TF32 operands.
+template <int NT, int MODE, int SPLIT>
+__device__ inline void convert_stage(const unsigned char* rb, unsigned char* cv, int ct) {
+    using RG = Ring<NT>;
+    constexpr bool TR = (MODE == BA || MODE == BB);
+    for (int id = ct; id < MR * 4; id += NCONV) {   // factor operand: 128 rows x 16 k, (row, 4 consecutive k)
+        const int row = id & 127, kq = id >> 7;
+        const int oi = row >> 5, r = row & 31;
+        float re[4], im[4];
+        if (!TR) {
+            const float2* src = (const float2*)(rb + oi * 4096);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { float2 a = src[(4 * kq + j) * 32 + r]; re[j] = a.x; im[j] = a.y; }
+        } else {
+            const float4* src = (const float4*)(rb + oi * 32 * TROW + r * TROW + kq * 32);
+            float4 a0 = src[0], a1 = src[1];
+            re[0] = a0.x; im[0] = a0.y; re[1] = a0.z; im[1] = a0.w;
+            re[2] = a1.x; im[2] = a1.y; re[3] = a1.z; im[3] = a1.w;
+        }
+        float4 rh, ih;
+        rh.x = tf32_hi(re[0]); rh.y = tf32_hi(re[1]); rh.z = tf32_hi(re[2]); rh.w = tf32_hi(re[3]);
+        ih.x = tf32_hi(im[0]); ih.y = tf32_hi(im[1]); ih.z = tf32_hi(im[2]); ih.w = tf32_hi(im[3]);
+        const int off = coff(row, 4 * kq);
+        *(float4*)(cv + 0 * RG::A_MAT + off) = rh;
+        *(float4*)(cv + 2 * RG::A_MAT + off) = ih;
+        if (SPLIT == 3) {
+            *(float4*)(cv + 1 * RG::A_MAT + off) = make_float4(re[0] - rh.x, re[1] - rh.y, re[2] - rh.z, re[3] - rh.w);
+            *(float4*)(cv + 3 * RG::A_MAT + off) = make_float4(im[0] - ih.x, im[1] - ih.y, im[2] - ih.z, im[3] - ih.w);
+        }
+    }
+    for (int id = ct; id < NT * 4; id += NCONV) {   // vector operand: NT rows x 16 k
+        const int n = id % NT, kq = id / NT;
+        const float2* src = (const float2*)(rb + RG::RAW_A);
+        float re[4], im[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { float2 a = src[(4 * kq + j) * NT + n]; re[j] = a.x; im[j] = a.y; }
+        float4 rh, ih;
+        rh.x = tf32_hi(re[0]); rh.y = tf32_hi(re[1]); rh.z = tf32_hi(re[2]); rh.w = tf32_hi(re[3]);
+        ih.x = tf32_hi(im[0]); ih.y = tf32_hi(im[1]); ih.z = tf32_hi(im[2]); ih.w = tf32_hi(im[3]);
+        const int off = 4 * RG::A_MAT + coff(n, 4 * kq);
+        *(float4*)(cv + off + 0 * RG::X_MAT) = rh;
+        *(float4*)(cv + off + 2 * RG::X_MAT) = ih;
+        if (SPLIT == 3) {
+            *(float4*)(cv + off + 1 * RG::X_MAT) = make_float4(re[0] - rh.x, re[1] - rh.y, re[2] - rh.z, re[3] - rh.w);
+            *(float4*)(cv + off + 3 * RG::X_MAT) = make_float4(im[0] - ih.x, im[1] - ih.y, im[2] - ih.z, im[3] - ih.w);
+        }
+    }
+}
+
+// MMA part of a stage (one thread): 2 x (4 or 12) MMAs of 8 complex reduction indices.
+template <int NT, int SPLIT>
+__device__ inline void mma_stage(uint32_t base, uint32_t tm_r, uint32_t tm_i, bool first_stage) {
+    using RG = Ring<NT>;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(MR >> 4) << 24);
+    const uint32_t idesc_neg = idesc | (1u << 13);
+#pragma unroll
+    for (int ks = 0; ks < KC / 8; ++ks) {
+        const uint32_t ko = ks * 2 * LBO;
+        const uint64_t arh = smem_desc(base + 0 * RG::A_MAT + ko), arl = smem_desc(base + 1 * RG::A_MAT + ko);
+        const uint64_t aih = smem_desc(base + 2 * RG::A_MAT + ko), ail = smem_desc(base + 3 * RG::A_MAT + ko);
+        const uint32_t xb = base + 4 * RG::A_MAT + ko;
+        const uint64_t xrh = smem_desc(xb), xrl = smem_desc(xb + RG::X_MAT);
+        const uint64_t xih = smem_desc(xb + 2 * RG::X_MAT), xil = smem_desc(xb + 3 * RG::X_MAT);
+        const uint32_t first = (first_stage && ks == 0) ? 0u : 1u;
+        mma_tf32(tm_r, arh, xrh, idesc, first);      // Yr = Ar Xr - Ai Xi
+        mma_tf32(tm_r, aih, xih, idesc_neg, 1u);
+        mma_tf32(tm_i, aih, xrh, idesc, first);      // Yi = Ai Xr + Ar Xi
+        mma_tf32(tm_i, arh, xih, idesc, 1u);
+        if (SPLIT == 3) {                             // hi x lo and lo x hi terms
+            mma_tf32(tm_r, arh, xrl, idesc, 1u);
+            mma_tf32(tm_r, arl, xrh, idesc, 1u);
+            mma_tf32(tm_r, aih, xil, idesc_neg, 1u);
+            mma_tf32(tm_r, ail, xih, idesc_neg, 1u);
+            mma_tf32(tm_i, aih, xrl, idesc, 1u);
+            mma_tf32(tm_i, ail, xrh, idesc, 1u);
+            mma_tf32(tm_i, arh, xil, idesc, 1u);
+            mma_tf32(tm_i, arl, xih, idesc, 1u);
+        }
+    }
+}
+
+// Writes one 16-byte column pair y of an output row (global offset base + c) by the output rule.
+template <int MODE>
+__device__ inline void write_pair(const Item& it, long long base, int c, float4 y, float2 d, float4 z) {
+    float4* dx = (float4*)(it.jb.x + base + c);
+    float4* da = (float4*)(it.jb.acc + base + c);
+    if (MODE == FB) {
+        atomicAdd(da, make_float4(-y.x, -y.y, -y.z, -y.w));
+    } else if (MODE == FA || MODE == BB) {
+        if (it.unique) *dx = y;
+        else atomicAdd(dx, y);
+    } else {  // BA: acc = Dinv z - partial; the first split clears z
+        if (it.kbeg == 0) {
+            y.x -= d.x * z.x - d.y * z.y; y.y -= d.x * z.y + d.y * z.x;
+            y.z -= d.x * z.z - d.y * z.w; y.w -= d.x * z.w + d.y * z.z;
+            *dx = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const float4 ny = make_float4(-y.x, -y.y, -y.z, -y.w);
+        if (it.unique) *da = ny;
+        else atomicAdd(da, ny);
+    }
+}
+
+// global offset (row x ldc + chunk column) of local output row r of an item, -1 if absent
+template <int MODE>
+__device__ inline long long row_base(const Item& it, int r, int ldc) {
+    const int row = it.o0 * TILE + r;
+    if ((it.o0 + (r >> 5)) >= it.nout_t || row >= it.nrows_out) return -1;
+    const int* upd = it.jb.upd_idx + it.nd.upd_off;
+    return ((MODE == FB) ? (long long)upd[row] : (long long)(it.nd.own0 + row)) * ldc + it.col0;
+}
+
+// ------------------------------------------------------------------------------------------
+// k_subst_tc: one block per work item
+// ------------------------------------------------------------------------------------------
+template <int NT> struct OneLayout {
+    using RG = Ring<NT>;
+    static constexpr int NTHREADS = NLOAD + NCONV + 32;
+    static constexpr int HALF = NT / 2;                  // output columns staged per epilogue pass
+    static constexpr int SP = HALF + 2;                  // staging pitch (complex): 16-byte rows, odd in 16 B
+    static_assert(MR * SP * 8 <= RG::BYTES, "staging tile must fit in the ring buffers");
+    static constexpr int ROWS_OFF = RG::BYTES;           // long long rowbase[128], float2 dinv[128]
+    static constexpr int BAR_OFF = ROWS_OFF + MR * 8 + MR * 8;
+    static constexpr int TOTAL = BAR_OFF + 8 * 8 + 16;
+};
 
 template <int NT, int MODE, int SPLIT>
-__global__ void __launch_bounds__(NTHREADS, 1) k_subst_tc(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ jobs,
-                                                          int ldc, int nchunks, int KS, int* flag) {
-    using LY = Layout<NT>;
-    constexpr bool TR = (MODE == BA || MODE == BB);  // factor tiles used transposed
+__global__ void __launch_bounds__(OneLayout<NT>::NTHREADS, 1)
+k_subst_tc(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ jobs, int ldc, int nchunks, int KS,
+           int* flag) {
+    using RG = Ring<NT>;
+    using LY = OneLayout<NT>;
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* conv = smem;
-    unsigned char* raw = smem + 2 * LY::CONV;
-    uint64_t* bars = (uint64_t*)(raw + 2 * LY::RAW);
-    uint64_t* raw_full = bars + 0;    // [2] loaders' copies landed (count NLOAD)
-    uint64_t* raw_empty = bars + 2;   // [2] converters done reading (count NCONVT)
-    uint64_t* conv_full = bars + 4;   // [2] converted operands written (count NCONVT)
+    unsigned char* conv = smem;                  // [2][CONV]
+    unsigned char* raw = smem + 2 * RG::CONV;    // [2][RAW]
+    long long* rowbase = (long long*)(smem + LY::ROWS_OFF);
+    float2* dinv_s = (float2*)(smem + LY::ROWS_OFF + MR * 8);
+    uint64_t* bars = (uint64_t*)(smem + LY::BAR_OFF);
+    uint64_t* raw_full = bars;        // [2] loaders' copies landed (count NLOAD)
+    uint64_t* raw_empty = bars + 2;   // [2] converters done reading (count NCONV)
+    uint64_t* conv_full = bars + 4;   // [2] converted operands written (count NCONV)
     uint64_t* conv_empty = bars + 6;  // [2] MMAs of the buffer done (tcgen05.commit)
     uint32_t* tptr = (uint32_t*)(bars + 8);
+    volatile int* abort = (volatile int*)(bars + 8) + 1;
 
-    const int chunk = blockIdx.x % nchunks;
-    const Task tk = tasks[blockIdx.x / nchunks];
-    const JobDev<float2> jb = jobs[tk.job];
-    const NodeDev nd = jb.nodes[tk.node];
+    const Item it = decode<NT, MODE>(tasks, jobs, blockIdx.x, nchunks, KS);
     const int t = threadIdx.x, w = t >> 5, l = t & 31;
-    const int col0 = chunk * NT;
-    const int o0 = tk.tile;  // first of the four output tiles
-    const int nout_t = (MODE == FB) ? nd.upd_t : nd.own_t;
-    const int kbeg = tk.pad_;
-    const int kend = min((MODE == FA) ? min(o0 + 4, nd.own_t) : ((MODE == BA) ? nd.upd_t : nd.own_t), kbeg + KS);
-    const int nst = max(0, kend - kbeg) * 2;
-    const float2* vec = (MODE == FA || MODE == BB) ? jb.acc : jb.x;
-    const int* upd = jb.upd_idx + nd.upd_off;
-    const int nrows_k = (MODE == BA) ? nd.nupd : nd.nown;   // valid vector rows
-    const int mma_warp = (NLOAD + NCONVT) / 32;
+    const int nst = it.nst;
+    const int mma_warp = (NLOAD + NCONV) / 32;
 
     if (w == mma_warp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(tptr)), "r"(2 * NT));
@@ -153,10 +386,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_subst_tc(const Task* __restrict
     if (t == 0) {
         for (int b = 0; b < 2; ++b) {
             mbar_init(raw_full + b, NLOAD);
-            mbar_init(raw_empty + b, NCONVT);
-            mbar_init(conv_full + b, NCONVT);
+            mbar_init(raw_empty + b, NCONV);
+            mbar_init(conv_full + b, NCONV);
             mbar_init(conv_empty + b, 1);
         }
+        *abort = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -166,154 +400,50 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_subst_tc(const Task* __restrict
     bool ok = true;
 
     if (t < NLOAD) {
-        // ------------------------------------------------------------ loaders
         for (int s = 0; s < nst && ok; ++s) {
-            const int slot = s & 1;
-            if (s >= 2) ok = mbar_wait(smem_u32(raw_empty + slot), (uint32_t)(((s >> 1) - 1) & 1));
+            const int slot = s & 1, use = s >> 1;
+            if (s >= 2) ok = mbar_wait(smem_u32(raw_empty + slot), (uint32_t)((use - 1) & 1), abort);
             if (!ok) break;
-            unsigned char* rb = raw + slot * LY::RAW;
-            const int kt = kbeg + (s >> 1), hk = s & 1;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {     // factor tiles: 1024 chunks of 16 bytes
-                const int c = t + NLOAD * i;
-                const int oi = c >> 8, q = c & 255;
-                const int o = o0 + oi;
-                bool exists = o < nout_t;
-                if (MODE == FA) exists = exists && kt <= o;
-                if (MODE == BB) exists = exists && kt >= o;
-                long long toff = 0;
-                if (exists) {
-                    if (MODE == FA) toff = nd.linv_off + tri_idx(o, kt);
-                    else if (MODE == FB) toff = nd.l21_off + (long long)o * nd.own_t + kt;
-                    else if (MODE == BA) toff = nd.l21_off + (long long)kt * nd.own_t + o;
-                    else toff = nd.linv_off + tri_idx(kt, o);
-                }
-                const float2* tl = jb.fac + toff * TILE2;
-                uint32_t dst;
-                const float2* src;
-                if (!TR) {
-                    dst = smem_u32(rb + oi * 4096 + q * 16);
-                    src = tl + hk * KC * 32 + q * 2;
-                } else {
-                    const int r = q >> 3, j = q & 7;
-                    dst = smem_u32(rb + oi * 32 * TROW + r * TROW + j * 16);
-                    src = tl + 32 * r + hk * KC + j * 2;
-                }
-                cp16(dst, exists ? (const void*)src : (const void*)jb.fac, exists ? 16 : 0);
-            }
-            for (int c = t; c < KC * NT / 2; c += NLOAD) {  // vector rows: KC x NT, raw [k][n]
-                const int k = c / (NT / 2), j = c % (NT / 2);
-                const int rr = kt * TILE + hk * KC + k;
-                const bool v = rr < nrows_k;
-                long long row = 0;
-                if (v) row = (MODE == BA) ? (long long)upd[rr] : (long long)(nd.own0 + rr);
-                cp16(smem_u32(rb + LY::RAW_A + k * NT * 8 + j * 16), vec + row * ldc + col0 + 2 * j, v ? 16 : 0);
-            }
+            load_stage<NT, MODE>(raw + slot * RG::RAW, it, s, ldc, t);
             cp_async_arrive(raw_full + slot);
         }
+        // row descriptors of the epilogue, fetched while the pipeline drains
+        for (int r = t; r < MR; r += NLOAD) {
+            const long long base = row_base<MODE>(it, r, ldc);
+            rowbase[r] = base;
+            if (MODE == BA) dinv_s[r] = base >= 0 ? it.jb.dinv[it.nd.own0 + it.o0 * TILE + r] : make_float2(0.f, 0.f);
+        }
         asm volatile("cp.async.wait_all;" ::: "memory");
-    } else if (t < NLOAD + NCONVT) {
-        // ------------------------------------------------------------ converters
+    } else if (t < NLOAD + NCONV) {
         const int ct = t - NLOAD;
         for (int s = 0; s < nst && ok; ++s) {
-            const int slot = s & 1;
-            ok = mbar_wait(smem_u32(raw_full + slot), (uint32_t)((s >> 1) & 1));
-            if (ok && s >= 2) ok = mbar_wait(smem_u32(conv_empty + slot), (uint32_t)(((s >> 1) - 1) & 1));
+            const int slot = s & 1, use = s >> 1;
+            ok = mbar_wait(smem_u32(raw_full + slot), (uint32_t)(use & 1), abort);
+            if (ok && s >= 2) ok = mbar_wait(smem_u32(conv_empty + slot), (uint32_t)((use - 1) & 1), abort);
             if (!ok) break;
-            unsigned char* rb = raw + slot * LY::RAW;
-            unsigned char* cv = conv + slot * LY::CONV;
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {     // factor operand: 128 rows x 16 k, (row, 4 consecutive k)
-                const int id = ct + NCONVT * i;
-                const int row = id & 127, kq = id >> 7;
-                const int oi = row >> 5, r = row & 31;
-                float re[4], im[4];
-                if (!TR) {
-                    const float2* src = (const float2*)(rb + oi * 4096);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) { float2 a = src[(4 * kq + j) * 32 + r]; re[j] = a.x; im[j] = a.y; }
-                } else {
-                    const float4* src = (const float4*)(rb + oi * 32 * TROW + r * TROW + kq * 32);
-                    float4 a0 = src[0], a1 = src[1];
-                    re[0] = a0.x; im[0] = a0.y; re[1] = a0.z; im[1] = a0.w;
-                    re[2] = a1.x; im[2] = a1.y; re[3] = a1.z; im[3] = a1.w;
-                }
-                float4 rh, ih;
-                rh.x = tf32_hi(re[0]); rh.y = tf32_hi(re[1]); rh.z = tf32_hi(re[2]); rh.w = tf32_hi(re[3]);
-                ih.x = tf32_hi(im[0]); ih.y = tf32_hi(im[1]); ih.z = tf32_hi(im[2]); ih.w = tf32_hi(im[3]);
-                const int off = coff(row, 4 * kq);
-                *(float4*)(cv + 0 * LY::A_MAT + off) = rh;
-                *(float4*)(cv + 2 * LY::A_MAT + off) = ih;
-                if (SPLIT == 3) {
-                    *(float4*)(cv + 1 * LY::A_MAT + off) = make_float4(re[0] - rh.x, re[1] - rh.y, re[2] - rh.z, re[3] - rh.w);
-                    *(float4*)(cv + 3 * LY::A_MAT + off) = make_float4(im[0] - ih.x, im[1] - ih.y, im[2] - ih.z, im[3] - ih.w);
-                }
-            }
-            for (int id = ct; id < NT * 4; id += NCONVT) {   // vector operand: NT rows x 16 k
-                const int n = id % NT, kq = id / NT;
-                const float2* src = (const float2*)(rb + LY::RAW_A);
-                float re[4], im[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) { float2 a = src[(4 * kq + j) * NT + n]; re[j] = a.x; im[j] = a.y; }
-                float4 rh, ih;
-                rh.x = tf32_hi(re[0]); rh.y = tf32_hi(re[1]); rh.z = tf32_hi(re[2]); rh.w = tf32_hi(re[3]);
-                ih.x = tf32_hi(im[0]); ih.y = tf32_hi(im[1]); ih.z = tf32_hi(im[2]); ih.w = tf32_hi(im[3]);
-                const int off = 4 * LY::A_MAT + coff(n, 4 * kq);
-                *(float4*)(cv + off + 0 * LY::X_MAT) = rh;
-                *(float4*)(cv + off + 2 * LY::X_MAT) = ih;
-                if (SPLIT == 3) {
-                    *(float4*)(cv + off + 1 * LY::X_MAT) = make_float4(re[0] - rh.x, re[1] - rh.y, re[2] - rh.z, re[3] - rh.w);
-                    *(float4*)(cv + off + 3 * LY::X_MAT) = make_float4(im[0] - ih.x, im[1] - ih.y, im[2] - ih.z, im[3] - ih.w);
-                }
-            }
+            convert_stage<NT, MODE, SPLIT>(raw + slot * RG::RAW, conv + slot * RG::CONV, ct);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(raw_empty + slot);
             mbar_arrive(conv_full + slot);
         }
     } else if (l == 0) {
-        // ------------------------------------------------------------ MMA issuer
-        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(MR >> 4) << 24);
-        const uint32_t idesc_neg = idesc | (1u << 13);
         for (int s = 0; s < nst && ok; ++s) {
-            const int cb = s & 1;
-            ok = mbar_wait(smem_u32(conv_full + cb), (uint32_t)((s >> 1) & 1));
+            const int cb = s & 1, use = s >> 1;
+            ok = mbar_wait(smem_u32(conv_full + cb), (uint32_t)(use & 1), abort);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t base = smem_u32(conv + cb * LY::CONV);
-#pragma unroll
-            for (int ks = 0; ks < KC / 8; ++ks) {
-                const uint32_t ko = ks * 2 * LBO;
-                const uint64_t arh = smem_desc(base + 0 * LY::A_MAT + ko), arl = smem_desc(base + 1 * LY::A_MAT + ko);
-                const uint64_t aih = smem_desc(base + 2 * LY::A_MAT + ko), ail = smem_desc(base + 3 * LY::A_MAT + ko);
-                const uint32_t xb = base + 4 * LY::A_MAT + ko;
-                const uint64_t xrh = smem_desc(xb), xrl = smem_desc(xb + LY::X_MAT);
-                const uint64_t xih = smem_desc(xb + 2 * LY::X_MAT), xil = smem_desc(xb + 3 * LY::X_MAT);
-                const uint32_t first = (s == 0 && ks == 0) ? 0u : 1u;
-                mma_tf32(tm_r, arh, xrh, idesc, first);      // Yr = Ar Xr - Ai Xi
-                mma_tf32(tm_r, aih, xih, idesc_neg, 1u);
-                mma_tf32(tm_i, aih, xrh, idesc, first);      // Yi = Ai Xr + Ar Xi
-                mma_tf32(tm_i, arh, xih, idesc, 1u);
-                if (SPLIT == 3) {                             // hi x lo and lo x hi terms
-                    mma_tf32(tm_r, arh, xrl, idesc, 1u);
-                    mma_tf32(tm_r, arl, xrh, idesc, 1u);
-                    mma_tf32(tm_r, aih, xil, idesc_neg, 1u);
-                    mma_tf32(tm_r, ail, xih, idesc_neg, 1u);
-                    mma_tf32(tm_i, aih, xrl, idesc, 1u);
-                    mma_tf32(tm_i, ail, xrh, idesc, 1u);
-                    mma_tf32(tm_i, arh, xil, idesc, 1u);
-                    mma_tf32(tm_i, arl, xih, idesc, 1u);
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(smem_u32(conv_empty + cb)));
+            mma_stage<NT, SPLIT>(smem_u32(conv + cb * RG::CONV), tm_r, tm_i, s == 0);
+            mma_commit(conv_empty + cb);
         }
     }
 
     // every role arrives here (their waits are bounded); make the outcome block-uniform
     ok = __syncthreads_and(ok) != 0;
     bool done = true;
-    if (nst > 0) {
-        const bool got = mbar_wait(smem_u32(conv_empty + ((nst - 1) & 1)), (uint32_t)(((nst - 1) >> 1) & 1));
+    if (nst > 0) {   // the last stage's MMAs, waited for even after an abort
+        const int sl = nst - 1;
+        int no_abort = 0;
+        const bool got = mbar_wait(smem_u32(conv_empty + (sl & 1)), (uint32_t)((sl >> 1) & 1), &no_abort);
         done = __syncthreads_and(got) != 0;
     }
     if (!ok || !done) {
@@ -322,96 +452,60 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_subst_tc(const Task* __restrict
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-    // ---- epilogue (converter warps), in two passes so that global memory sees whole rows:
-    //  (1) tensor memory -> shared staging tile [128 rows][NT + 2] (warp w reads lanes
-    //      32 (w % 4) .. +31 = output tile o0 + w % 4, column half by the converter-warp index);
-    //  (2) each converter warp writes 16 staged rows, lane = pair of columns (16-byte accesses).
-    //  A task that covers the whole reduction of its outputs is their only writer and stores;
-    //  split reductions (and FB, whose update rows are shared between nodes) accumulate.
-    if (ok && t >= NLOAD && t < NLOAD + NCONVT) {
-        constexpr int SP = NT + 2;           // staging pitch (complex): 16-byte rows, odd in 16-byte units
-        float2* stg = (float2*)smem;         // operand and raw buffers are free once the MMAs are done
-        const int cw = (t - NLOAD) >> 5;     // converter warp 0..7
-        {
-            const int q4 = w & 3;
-            const int rl = 32 * q4 + l;
-            const int cbeg = (cw >> 2) * (NT / 2);
-            for (int c0 = cbeg; c0 < cbeg + NT / 2; c0 += 16) {
+    // ---- epilogue (converter warps), per column half of the tile:
+    //  (1) tensor memory -> shared staging tile [128 rows][HALF + 2]; warp w may read TMEM lanes
+    //      32 (w % 4) .. +31 (output tile o0 + w % 4); the two warps of a lane quarter split the columns;
+    //  (2) each converter warp writes 16 staged rows, lane = pair of columns (16-byte accesses),
+    //      all loads of a batch of rows (BA's z) before its writes.
+    if (ok && t >= NLOAD && t < NLOAD + NCONV) {
+        constexpr int HALF = LY::HALF, SP = LY::SP;
+        constexpr int CPW = HALF / 2;            // columns per warp per pass
+        constexpr int RPW = MR / (NCONV / 32);   // staged rows written per warp
+        constexpr int NP = HALF / 2;             // 16-byte column pairs per row and pass
+        constexpr int RB = 8;                    // rows per load batch
+        static_assert(CPW % 16 == 0 && RPW % RB == 0, "epilogue tiling");
+        float2* stg = (float2*)smem;             // operand and raw buffers are free after the MMAs
+        const int cw = (t - NLOAD) >> 5;
+        const int q4 = w & 3, sub = cw >> 2;
+        const int rl = 32 * q4 + l;
+        for (int pass = 0; pass < 2; ++pass) {
+            const int cbeg = pass * HALF + sub * CPW;
+            for (int c0 = cbeg; c0 < cbeg + CPW; c0 += 16) {
                 uint32_t vr[16], vi[16];
                 if (nst > 0) {
                     const uint32_t lane_off = (uint32_t)(32 * q4) << 16;
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                                 : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]), "=r"(vr[7]),
-                                   "=r"(vr[8]), "=r"(vr[9]), "=r"(vr[10]), "=r"(vr[11]), "=r"(vr[12]), "=r"(vr[13]), "=r"(vr[14]), "=r"(vr[15])
-                                 : "r"(tm_r + lane_off + (uint32_t)c0));
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                                 : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]), "=r"(vi[7]),
-                                   "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]), "=r"(vi[13]), "=r"(vi[14]), "=r"(vi[15])
-                                 : "r"(tm_i + lane_off + (uint32_t)c0));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    tmem_ld16(tm_r + lane_off + (uint32_t)c0, tm_i + lane_off + (uint32_t)c0, vr, vi);
                 } else {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) { vr[j] = 0u; vi[j] = 0u; }
                 }
+                const int cl = c0 - pass * HALF;
 #pragma unroll
                 for (int j = 0; j < 16; j += 2)
-                    *(float4*)&stg[rl * SP + c0 + j] = make_float4(__uint_as_float(vr[j]), __uint_as_float(vi[j]),
+                    *(float4*)&stg[rl * SP + cl + j] = make_float4(__uint_as_float(vr[j]), __uint_as_float(vi[j]),
                                                                    __uint_as_float(vr[j + 1]), __uint_as_float(vi[j + 1]));
             }
-        }
-        asm volatile("bar.sync 1, %0;" :: "n"(NCONVT) : "memory");   // converter warps only
-
-        const int kfull0 = (MODE == BB) ? o0 : 0;
-        const int kfull1 = (MODE == FA) ? min(o0 + 4, nd.own_t) : ((MODE == BA) ? nd.upd_t : nd.own_t);
-        const bool unique = kbeg == kfull0 && kend == kfull1 && MODE != FB;
-        const int nrows_out = (MODE == FB) ? nd.nupd : nd.nown;
-        constexpr int RB = 4, NV = NT / 64;  // rows per batch; 16-byte column pairs per lane and row
-        for (int i0 = 0; i0 < 16; i0 += RB) {
-            long long base[RB];
-            bool vrow[RB];
-            float2 di[RB];
-            float4 z[RB][NV];
-            // all loads of the batch first (row indices, D^{-1}, z), then the writes
+            asm volatile("bar.sync 1, %0;" :: "n"(NCONV) : "memory");   // converter warps only
+            const bool lane_on = l < NP;
+            const int c = pass * HALF + 2 * l;
+            for (int i0 = 0; i0 < RPW; i0 += RB) {
+                float4 z[RB];
 #pragma unroll
-            for (int r = 0; r < RB; ++r) {
-                const int rl2 = cw * 16 + i0 + r;
-                const int row = o0 * TILE + rl2;
-                vrow[r] = (o0 + (rl2 >> 5)) < nout_t && row < nrows_out;
-                base[r] = 0;
-                if (vrow[r]) base[r] = ((MODE == FB) ? (long long)upd[row] : (long long)(nd.own0 + row)) * ldc + col0;
-                if (MODE == BA && kbeg == 0 && vrow[r]) {
-                    di[r] = jb.dinv[nd.own0 + row];
+                for (int r = 0; r < RB; ++r) {
+                    z[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    const long long base = rowbase[cw * RPW + i0 + r];
+                    if (MODE == BA && it.kbeg == 0 && lane_on && base >= 0) z[r] = *(const float4*)(it.jb.x + base + c);
+                }
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) z[r][v] = *(const float4*)(jb.x + base[r] + 2 * l + 64 * v);
+                for (int r = 0; r < RB; ++r) {
+                    const int rl2 = cw * RPW + i0 + r;
+                    const long long base = rowbase[rl2];
+                    if (!lane_on || base < 0) continue;
+                    const float2 d = (MODE == BA) ? dinv_s[rl2] : make_float2(0.f, 0.f);
+                    write_pair<MODE>(it, base, c, *(const float4*)&stg[rl2 * SP + 2 * l], d, z[r]);
                 }
             }
-#pragma unroll
-            for (int r = 0; r < RB; ++r) {
-                if (!vrow[r]) continue;
-                const int rl2 = cw * 16 + i0 + r;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    const int c = 2 * l + 64 * v;
-                    float4 y = *(const float4*)&stg[rl2 * SP + c];
-                    if (MODE == FB) {
-                        atomicAdd((float4*)(jb.acc + base[r] + c), make_float4(-y.x, -y.y, -y.z, -y.w));
-                    } else if (MODE == FA || MODE == BB) {
-                        if (unique) *(float4*)(jb.x + base[r] + c) = y;
-                        else atomicAdd((float4*)(jb.x + base[r] + c), y);
-                    } else {  // BA: acc = Dinv z - partial; the first split clears z
-                        if (kbeg == 0) {
-                            const float2 d = di[r];
-                            const float4 q = z[r][v];
-                            y.x -= d.x * q.x - d.y * q.y; y.y -= d.x * q.y + d.y * q.x;
-                            y.z -= d.x * q.z - d.y * q.w; y.w -= d.x * q.w + d.y * q.z;
-                            *(float4*)(jb.x + base[r] + c) = make_float4(0.f, 0.f, 0.f, 0.f);
-                        }
-                        const float4 ny = make_float4(-y.x, -y.y, -y.z, -y.w);
-                        if (unique) *(float4*)(jb.acc + base[r] + c) = ny;
-                        else atomicAdd((float4*)(jb.acc + base[r] + c), ny);
-                    }
-                }
-            }
+            asm volatile("bar.sync 1, %0;" :: "n"(NCONV) : "memory");   // staging reused by the next pass
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -419,17 +513,231 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_subst_tc(const Task* __restrict
     if (w == mma_warp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(2 * NT));
 }
 
+// ------------------------------------------------------------------------------------------
+// k_subst_tcp: persistent, one block per SM
+// ------------------------------------------------------------------------------------------
+template <int NT> struct PLayout {
+    using RG = Ring<NT>;
+    static constexpr int NEPI = 128;                       // epilogue threads (4 warps)
+    static constexpr int NTHREADS = NLOAD + NCONV + 32 + NEPI;
+    static constexpr int EP = 18;                          // staging pitch (complex) of a 32 x 16 chunk
+    static constexpr int STG_OFF = RG::BYTES;              // 4 warps x 32 rows x EP complex
+    static constexpr int BAR_OFF = STG_OFF + 4 * 32 * EP * 8;
+    static constexpr int TOTAL = BAR_OFF + 12 * 8 + 16;
+    static constexpr int TMEM_COLS = 4 * NT;               // two accumulator buffers (re, im) x NT
+};
+
 template <int NT, int MODE, int SPLIT>
-void launch_one(const Task* tasks, long long n, const JobDev<float2>* jobs, int ldc, int KS, int* flag, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        HZ_CUDA(cudaFuncSetAttribute(k_subst_tc<NT, MODE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     Layout<NT>::TOTAL));
-        attr = true;
+__global__ void __launch_bounds__(PLayout<NT>::NTHREADS, 1)
+k_subst_tcp(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ jobs, int ldc, int nchunks, int KS,
+            long long nitems, int* flag) {
+    using RG = Ring<NT>;
+    using LY = PLayout<NT>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* conv = smem;                  // [2][CONV]
+    unsigned char* raw = smem + 2 * RG::CONV;    // [2][RAW]
+    uint64_t* bars = (uint64_t*)(smem + LY::BAR_OFF);
+    uint64_t* raw_full = bars;         // [2] loaders' copies landed (count NLOAD)
+    uint64_t* raw_empty = bars + 2;    // [2] converters done reading (count NCONV)
+    uint64_t* conv_full = bars + 4;    // [2] converted operands written (count NCONV)
+    uint64_t* conv_empty = bars + 6;   // [2] MMAs of the buffer done (tcgen05.commit)
+    uint64_t* acc_full = bars + 8;     // [2] all MMAs of an item's accumulator done (tcgen05.commit)
+    uint64_t* acc_empty = bars + 10;   // [2] epilogue done reading the accumulator (count NEPI)
+    uint32_t* tptr = (uint32_t*)(bars + 12);
+    volatile int* abort = (volatile int*)(bars + 12) + 1;
+
+    const int t = threadIdx.x, w = t >> 5, l = t & 31;
+    const int mma_warp = (NLOAD + NCONV) / 32;
+    const int epi_warp0 = (NLOAD + NCONV + 32) / 32;
+
+    if (w == mma_warp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(tptr)),
+                     "r"(LY::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    if (t == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(raw_full + b, NLOAD);
+            mbar_init(raw_empty + b, NCONV);
+            mbar_init(conv_full + b, NCONV);
+            mbar_init(conv_empty + b, 1);
+            mbar_init(acc_full + b, 1);
+            mbar_init(acc_empty + b, LY::NEPI);
+        }
+        *abort = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tptr;
+    bool ok = true;
+    bool mma_drained = true;
+
+    if (t < NLOAD) {
+        // ------------------------------------------------------------ loaders
+        long long gs = 0;  // stage counter across this block's items
+        for (long long item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            const Item it = decode<NT, MODE>(tasks, jobs, item, nchunks, KS);
+            for (int s = 0; s < it.nst && ok; ++s, ++gs) {
+                const int slot = (int)(gs & 1);
+                const long long use = gs >> 1;
+                if (gs >= 2) ok = mbar_wait(smem_u32(raw_empty + slot), (uint32_t)((use - 1) & 1), abort);
+                if (!ok) break;
+                load_stage<NT, MODE>(raw + slot * RG::RAW, it, s, ldc, t);
+                cp_async_arrive(raw_full + slot);
+            }
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (t < NLOAD + NCONV) {
+        // ------------------------------------------------------------ converters
+        const int ct = t - NLOAD;
+        long long gs = 0;
+        for (long long item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            const int nst = decode<NT, MODE>(tasks, jobs, item, nchunks, KS).nst;
+            for (int s = 0; s < nst && ok; ++s, ++gs) {
+                const int slot = (int)(gs & 1);
+                const long long use = gs >> 1;
+                ok = mbar_wait(smem_u32(raw_full + slot), (uint32_t)(use & 1), abort);
+                if (ok && gs >= 2) ok = mbar_wait(smem_u32(conv_empty + slot), (uint32_t)((use - 1) & 1), abort);
+                if (!ok) break;
+                convert_stage<NT, MODE, SPLIT>(raw + slot * RG::RAW, conv + slot * RG::CONV, ct);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(raw_empty + slot);
+                mbar_arrive(conv_full + slot);
+            }
+        }
+    } else if (w == mma_warp) {
+        // ------------------------------------------------------------ MMA issuer (lane 0)
+        if (l == 0) {
+            long long gs = 0;
+            int nit = 0;  // items of this block so far
+            for (long long item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++nit) {
+                const int nst = decode<NT, MODE>(tasks, jobs, item, nchunks, KS).nst;
+                const int b = nit & 1;
+                if (nit >= 2) ok = mbar_wait(smem_u32(acc_empty + b), (uint32_t)(((nit >> 1) - 1) & 1), abort);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t tm_r = tmem + (uint32_t)(b * 2 * NT), tm_i = tm_r + NT;
+                for (int s = 0; s < nst && ok; ++s, ++gs) {
+                    const int cb = (int)(gs & 1);
+                    ok = mbar_wait(smem_u32(conv_full + cb), (uint32_t)((gs >> 1) & 1), abort);
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    mma_stage<NT, SPLIT>(smem_u32(conv + cb * RG::CONV), tm_r, tm_i, s == 0);
+                    mma_commit(conv_empty + cb);
+                }
+                mma_commit(acc_full + b);   // arrives when every MMA issued so far has completed
+            }
+            // before the tensor memory is freed every issued MMA must have completed: the last
+            // item begun (nit - 1; an interrupted one was committed too) is waited for, even
+            // after an abort
+            if (nit > 0) {
+                int no_abort = 0;
+                mma_drained = mbar_wait(smem_u32(acc_full + ((nit - 1) & 1)), (uint32_t)(((nit - 1) >> 1) & 1), &no_abort);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue warps
+        // warp w reads TMEM lanes 32 (w % 4) .. +31 = output rows of tile o0 + w % 4 (lane = row);
+        // per 16-column chunk: stage 32 x 16 in this warp's shared slice, then write 4 rows per
+        // instruction (8 lanes x 16 bytes per row)
+        const int q4 = w & 3;
+        float2* stg = (float2*)(smem + LY::STG_OFF) + (size_t)(w - epi_warp0) * 32 * LY::EP;
+        const int r4 = l >> 3, p = l & 7;   // write phase: row within a group of 4, column pair
+        int nit = 0;
+        for (long long item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++nit) {
+            const Item it = decode<NT, MODE>(tasks, jobs, item, nchunks, KS);
+            const int b = nit & 1;
+            // this lane's row descriptor, shuffled to the writing lanes below
+            const long long my_base = row_base<MODE>(it, 32 * q4 + l, ldc);
+            float2 my_d = make_float2(0.f, 0.f);
+            if (MODE == BA && my_base >= 0) my_d = it.jb.dinv[it.nd.own0 + it.o0 * TILE + 32 * q4 + l];
+            ok = mbar_wait(smem_u32(acc_full + b), (uint32_t)((nit >> 1) & 1), abort);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t lane_off = (uint32_t)(32 * q4) << 16;
+            const uint32_t tm_r = tmem + (uint32_t)(b * 2 * NT) + lane_off, tm_i = tm_r + NT;
+            for (int c0 = 0; c0 < NT; c0 += 16) {
+                uint32_t vr[16], vi[16];
+                if (it.nst > 0) {
+                    tmem_ld16(tm_r + (uint32_t)c0, tm_i + (uint32_t)c0, vr, vi);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) { vr[j] = 0u; vi[j] = 0u; }
+                }
+#pragma unroll
+                for (int j = 0; j < 16; j += 2)
+                    *(float4*)&stg[l * LY::EP + j] = make_float4(__uint_as_float(vr[j]), __uint_as_float(vi[j]),
+                                                                 __uint_as_float(vr[j + 1]), __uint_as_float(vi[j + 1]));
+                __syncwarp();
+                const int c = c0 + 2 * p;
+                long long base[8];
+                float4 z[8];
+#pragma unroll
+                for (int g = 0; g < 8; ++g) {   // all loads of the chunk before its writes
+                    base[g] = __shfl_sync(0xffffffffu, my_base, 4 * g + r4);
+                    z[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (MODE == BA && it.kbeg == 0 && base[g] >= 0) z[g] = *(const float4*)(it.jb.x + base[g] + c);
+                }
+#pragma unroll
+                for (int g = 0; g < 8; ++g) {
+                    const int rr = 4 * g + r4;
+                    float2 d;
+                    d.x = __shfl_sync(0xffffffffu, my_d.x, rr);
+                    d.y = __shfl_sync(0xffffffffu, my_d.y, rr);
+                    if (base[g] < 0) continue;
+                    write_pair<MODE>(it, base[g], c, *(const float4*)&stg[rr * LY::EP + 2 * p], d, z[g]);
+                }
+                __syncwarp();
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(acc_empty + b);
+        }
+    }
+
+    ok = __syncthreads_and(ok && mma_drained) != 0;
+    if (!ok && t == 0) atomicExch(flag, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (w == mma_warp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(LY::TMEM_COLS));
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        HZ_CUDA(cudaGetDevice(&dev));
+        HZ_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return n;
+}
+
+template <int NT, int MODE, int SPLIT>
+void launch_one(const Batch& b, const Task* tasks, long long n, const JobDev<float2>* jobs, int ldc, int* flag,
+                cudaStream_t st) {
     const int nchunks = ldc / NT;
-    k_subst_tc<NT, MODE, SPLIT><<<(unsigned)(n * nchunks), NTHREADS, Layout<NT>::TOTAL, st>>>(tasks, jobs, ldc, nchunks,
-                                                                                               KS, flag);
+    const long long nitems = n * nchunks;
+    if (b.tc_cfg == 1) {
+        static bool attr = false;
+        if (!attr) {
+            HZ_CUDA(cudaFuncSetAttribute(k_subst_tcp<NT, MODE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         PLayout<NT>::TOTAL));
+            attr = true;
+        }
+        const long long grid = std::min<long long>(nitems, sm_count());
+        k_subst_tcp<NT, MODE, SPLIT><<<(unsigned)grid, PLayout<NT>::NTHREADS, PLayout<NT>::TOTAL, st>>>(
+            tasks, jobs, ldc, nchunks, b.KS_tc, nitems, flag);
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            HZ_CUDA(cudaFuncSetAttribute(k_subst_tc<NT, MODE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         OneLayout<NT>::TOTAL));
+            attr = true;
+        }
+        k_subst_tc<NT, MODE, SPLIT><<<(unsigned)nitems, OneLayout<NT>::NTHREADS, OneLayout<NT>::TOTAL, st>>>(
+            tasks, jobs, ldc, nchunks, b.KS_tc, flag);
+    }
     HZ_CHECK_LAUNCH();
 }
 
@@ -440,10 +748,10 @@ void launch_mode(const Batch& b, int h, int mode, int ldc, int* flag, cudaStream
     const Task* tasks = b.d_tasks + off;
     const JobDev<float2>* jobs = (const JobDev<float2>*)b.d_jobs;
     switch (mode) {
-        case FA: launch_one<NT, FA, SPLIT>(tasks, n, jobs, ldc, b.KS_tc, flag, st); break;
-        case FB: launch_one<NT, FB, SPLIT>(tasks, n, jobs, ldc, b.KS_tc, flag, st); break;
-        case BA: launch_one<NT, BA, SPLIT>(tasks, n, jobs, ldc, b.KS_tc, flag, st); break;
-        default: launch_one<NT, BB, SPLIT>(tasks, n, jobs, ldc, b.KS_tc, flag, st); break;
+        case FA: launch_one<NT, FA, SPLIT>(b, tasks, n, jobs, ldc, flag, st); break;
+        case FB: launch_one<NT, FB, SPLIT>(b, tasks, n, jobs, ldc, flag, st); break;
+        case BA: launch_one<NT, BA, SPLIT>(b, tasks, n, jobs, ldc, flag, st); break;
+        default: launch_one<NT, BB, SPLIT>(b, tasks, n, jobs, ldc, flag, st); break;
     }
 }
 

@@ -218,13 +218,16 @@ def test_solve_on_a_nonblocking_stream(hz):
     s.close()
 
 
+@pytest.mark.parametrize("cfg", ["0", "1"])
 @pytest.mark.parametrize("ncols", [64, 128, 130])
-def test_tensor_core_layer_solve(hz, ncols, monkeypatch):
+def test_tensor_core_layer_solve(hz, ncols, cfg, monkeypatch):
     """With the tensor-core path enabled, mixed-precision layer solves with >= 64 columns run on
     the tcgen05 kernel (split TF32); they must match the local direct solve within the stage
     tolerance."""
     monkeypatch.setenv("HZ_SUBST_TC", "1")
     monkeypatch.setenv("HZ_TC_MIN_TILES", "3")   # small fronts too: partial quads, masked rows
+    monkeypatch.setenv("HZ_TC_CFG", cfg)           # one block per work item (0) or persistent (1) ...
+    monkeypatch.setenv("HZ_AUTOTUNE", "0")         # ... as set, not as the autotuner would choose
     p = W.config(1)
     s = make_solver(hz, p, "mixed")
     parts = D.layer_partition(p.n, p.npml, p.n_layers)
@@ -323,6 +326,35 @@ def test_fast_preconditioner_solution_unchanged(hz, monkeypatch):
     ref = direct.solve(p.m, p.omega, p.npml, p.C, f[:2])
     assert rel(outs[1][:2], ref) < E2E_TOL["mixed"]
     assert iters[1] <= iters[0] + 2, iters
+
+
+def test_persistent_tensor_core_kernel_matches(hz, monkeypatch):
+    """The persistent tensor-core kernel (blocks walking several work items each, alternating
+    accumulator buffers, split reductions) gives the same M_pol and P as one block per work item
+    and as the CUDA-core kernels, on a 64^3 problem with 256 stacked columns."""
+    p = W.config(2)
+    rng = np.random.default_rng(123)
+    outs = {}
+    x = None
+    for name, env in (("simt", {"HZ_SUBST_TC": "0"}), ("tc0", {"HZ_SUBST_TC": "1", "HZ_TC_CFG": "0"}),
+                      ("tcp", {"HZ_SUBST_TC": "1", "HZ_TC_CFG": "1"})):
+        monkeypatch.setenv("HZ_AUTOTUNE", "0")
+        monkeypatch.setenv("HZ_TC_MIN_TILES", "2")
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        s = make_solver(hz, p, "mixed")
+        if x is None:
+            shp = s.trace_shape(64)
+            x = rng.standard_normal(shp) + 1j * rng.standard_normal(shp)
+        y = s.apply_mpol(cuda(x)).cpu().numpy()
+        z = s.apply_precond(cuda(x)).cpu().numpy()
+        outs[name] = (y, z)
+        s.close()
+    for name in ("tc0", "tcp"):
+        assert rel(outs[name][0], outs["simt"][0]) < 1e-4, name
+        assert rel(outs[name][1], outs["simt"][1]) < 1e-4, name
+    assert rel(outs["tcp"][0], outs["tc0"][0]) < 1e-5
+    assert rel(outs["tcp"][1], outs["tc0"][1]) < 1e-5
 
 
 def test_profile_detail_attributes_launches_by_kernel_kind(hz, small_case, monkeypatch):
