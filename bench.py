@@ -252,6 +252,8 @@ def run_ours(args):
     stream.synchronize()
     prof_step_ms = ep0.elapsed_time(ep1)
     kern = [s.profile_kernel(0), s.profile_kernel(1)]
+    if args.profile_levels:
+        print(s.profile_report(), file=sys.stderr, flush=True)
     smx = float(pk.get("sm_max_mhz", 2070.0))
     alu_peak = 152 * 128 * 2 * smx * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x max SM clock, TFLOP/s
     # TF32 tensor peak: the measured sustained bf16 GEMM rate x the nominal tf32/bf16 ratio (1.1/2.25)
@@ -480,6 +482,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--fp64-rhs", type=int, default=4)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-levels", action="store_true",
+                    help="print the per-phase, per-level substitution profile of the profiled solve (stderr)")
     ap.add_argument("--gmres-tol", type=float, default=1e-5)
     ap.add_argument("--refine-tol", type=float, default=1e-6)
     args = ap.parse_args()

@@ -110,7 +110,7 @@ void hz_default_opts(hz_precision prec, hz_solve_opts* opts);
  *   HZ_TC_CFG=1       with HZ_AUTOTUNE=0: the persistent tensor-core kernel (one block per SM
  *                     walking the work items) instead of one block per work item (0)
  *   HZ_AUTOTUNE=0     keep the fixed defaults; HZ_GRAPHS=0 no CUDA-graph replay;
- *   HZ_LEAF           nested-dissection leaf size (cells, default 64)
+ *   HZ_LEAF           nested-dissection leaf size (cells, default 256)
  */
 hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz_pml* pml,
                     int32_t n_layers, hz_precision prec, void* stream, hz_handle** out);
@@ -271,6 +271,12 @@ hz_status hz_profile_end(hz_handle* h, int64_t* calls, double* total_ms, double*
 hz_status hz_profile_kernel(hz_handle* h, int32_t kind, int64_t* launches, double* total_ms, double* alg_bytes,
                             double* alg_flops);
 int64_t hz_kernel_launches(void);
+
+/* Text table of the last detail-profiled interval (hz_profile_begin_detail .. hz_profile_end):
+ * one line per kernel kind, substitution phase (FA, FB, BA, BB) and tree level with its launches,
+ * work items (tasks, before the split into column chunks), summed device ms and algorithmic
+ * TFLOP/s.  The string stays valid until the next call on the handle. */
+const char* hz_profile_report(hz_handle* h);
 
 /* The substitution autotuner's record for this handle: one line per tuned batch signature
  * (layer shapes and column width) with the time of every candidate split-K depth and column

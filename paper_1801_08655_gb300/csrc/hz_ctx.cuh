@@ -3,6 +3,7 @@
 
 #include <functional>
 #include <map>
+#include <tuple>
 #include <memory>
 #include <string>
 #include <vector>
@@ -52,8 +53,8 @@ struct Batch {
 
 // Event-timed record of a substitution call (hz_profile_begin) or, in detail mode, of one
 // kernel launch of it (kind 0 CUDA-core, 1 tensor-core).
-struct ProfRec { cudaEvent_t e0, e1; double bytes, flops; int kind; };
-struct KernStat { long long launches = 0; double ms = 0, bytes = 0, flops = 0; };
+struct ProfRec { cudaEvent_t e0, e1; double bytes, flops; int kind, mode, level; long long tasks; };
+struct KernStat { long long launches = 0, tasks = 0; double ms = 0, bytes = 0, flops = 0; };
 
 // Recorded sequence of stream operations with the device descriptors it owns.  run() issues
 // the operations on a stream; run_graph() captures them once into a CUDA graph and replays it.
@@ -185,6 +186,8 @@ struct Ctx {
     bool prof_detail = false;                 // also time every substitution launch by kernel kind
     std::vector<ProfRec> prof_launch;
     KernStat kern_stat[2];                    // per kind, from the last hz_profile_end
+    std::map<std::tuple<int, int, int>, KernStat> kern_lvl;  // per (kind, phase, tree level)
+    std::string prof_text;
 };
 
 template <class C> void factor_layers(Ctx& ctx);

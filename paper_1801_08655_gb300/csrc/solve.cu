@@ -351,9 +351,14 @@ struct LaunchTimer {
     std::vector<ProfRec>* out;
     cudaStream_t st;
     ProfRec r{};
-    LaunchTimer(std::vector<ProfRec>* o, cudaStream_t s, int kind, double bytes, double flops) : out(o), st(s) {
+    LaunchTimer(std::vector<ProfRec>* o, cudaStream_t s, int kind, double bytes, double flops, int mode, int level,
+                long long tasks)
+        : out(o), st(s) {
         if (!out) return;
         r.kind = kind;
+        r.mode = mode;
+        r.level = level;
+        r.tasks = tasks;
         r.bytes = bytes;
         r.flops = flops;
         HZ_CUDA(cudaEventCreate(&r.e0));
@@ -371,12 +376,13 @@ template <class C, int CC>
 void run_batch(const Batch& b, int ldc, int ncols, bool tc, int* flag, cudaStream_t st, std::vector<ProfRec>* pl) {
     auto level = [&](int h, int mode) {
         if (b.cnt[mode][h] > 0) {
-            LaunchTimer lt(pl, st, 0, b.lvl_bytes[0][mode][h], b.lvl_flops[0][mode][h] * ncols);
+            LaunchTimer lt(pl, st, 0, b.lvl_bytes[0][mode][h], b.lvl_flops[0][mode][h] * ncols, mode, h, b.cnt[mode][h]);
             launch_level<C, CC>(b, h, mode, ldc, st);
             lt.done();
         }
         if (tc && b.pair_cnt[mode][h] > 0) {
-            LaunchTimer lt(pl, st, 1, b.lvl_bytes[1][mode][h], b.lvl_flops[1][mode][h] * ncols);
+            LaunchTimer lt(pl, st, 1, b.lvl_bytes[1][mode][h], b.lvl_flops[1][mode][h] * ncols, mode, h,
+                           b.pair_cnt[mode][h]);
             launch_level_tc(b, h, mode, ldc, flag, st);
             lt.done();
         }

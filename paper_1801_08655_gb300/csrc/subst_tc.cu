@@ -184,9 +184,29 @@ __device__ inline Item decode(const Task* tasks, const JobDev<float2>* jobs, lon
     return it;
 }
 
+// Vector rows a loader thread copies in stage s of an item (-1: beyond the node, zero-filled).
+// They are looked up one stage ahead, so that BA's gather through the update index list is not
+// on the copy's critical path.
+template <int NT> struct Vrows { int r[KC * NT / 2 / NLOAD]; };
+
+template <int NT, int MODE>
+__device__ inline Vrows<NT> stage_rows(const Item& it, int s, int t) {
+    Vrows<NT> v;
+    const int kt = it.kbeg + (s >> 1), hk = s & 1;
+    const int* upd = it.jb.upd_idx + it.nd.upd_off;
+#pragma unroll
+    for (int i = 0; i < KC * NT / 2 / NLOAD; ++i) {
+        const int k = (t + NLOAD * i) / (NT / 2);
+        const int rr = kt * TILE + hk * KC + k;
+        v.r[i] = -1;
+        if (rr < it.nrows_k) v.r[i] = (MODE == BA) ? upd[rr] : it.nd.own0 + rr;
+    }
+    return v;
+}
+
 // Loader part of stage s of an item: the four factor tiles' 16-column halves and 16 vector rows.
 template <int NT, int MODE>
-__device__ inline void load_stage(unsigned char* rb, const Item& it, int s, int ldc, int t) {
+__device__ inline void load_stage(unsigned char* rb, const Item& it, int s, int ldc, int t, const Vrows<NT>& vr) {
     using RG = Ring<NT>;
     constexpr bool TR = (MODE == BA || MODE == BB);  // factor tiles used transposed
     const NodeDev& nd = it.nd;
@@ -218,13 +238,12 @@ __device__ inline void load_stage(unsigned char* rb, const Item& it, int s, int 
         cp16(dst, exists ? (const void*)src : (const void*)it.jb.fac, exists ? 16 : 0);
     }
     const float2* vec = (MODE == FA || MODE == BB) ? it.jb.acc : it.jb.x;
-    const int* upd = it.jb.upd_idx + nd.upd_off;
-    for (int c = t; c < KC * NT / 2; c += NLOAD) {  // vector rows: KC x NT, raw [k][n]
+#pragma unroll
+    for (int i = 0; i < KC * NT / 2 / NLOAD; ++i) {  // vector rows: KC x NT, raw [k][n]
+        const int c = t + NLOAD * i;
         const int k = c / (NT / 2), j = c % (NT / 2);
-        const int rr = kt * TILE + hk * KC + k;
-        const bool v = rr < it.nrows_k;
-        long long row = 0;
-        if (v) row = (MODE == BA) ? (long long)upd[rr] : (long long)(nd.own0 + rr);
+        const bool v = vr.r[i] >= 0;
+        const long long row = v ? vr.r[i] : 0;
         cp16(smem_u32(rb + RG::RAW_A + k * NT * 8 + j * 16), vec + row * ldc + it.col0 + 2 * j, v ? 16 : 0);
     }
 }
@@ -400,12 +419,15 @@ k_subst_tc(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ jo
     bool ok = true;
 
     if (t < NLOAD) {
+        Vrows<NT> rows = stage_rows<NT, MODE>(it, 0, t);
         for (int s = 0; s < nst && ok; ++s) {
             const int slot = s & 1, use = s >> 1;
+            const Vrows<NT> next = stage_rows<NT, MODE>(it, s + 1, t);   // looked up ahead
             if (s >= 2) ok = mbar_wait(smem_u32(raw_empty + slot), (uint32_t)((use - 1) & 1), abort);
             if (!ok) break;
-            load_stage<NT, MODE>(raw + slot * RG::RAW, it, s, ldc, t);
+            load_stage<NT, MODE>(raw + slot * RG::RAW, it, s, ldc, t, rows);
             cp_async_arrive(raw_full + slot);
+            rows = next;
         }
         // row descriptors of the epilogue, fetched while the pipeline drains
         for (int r = t; r < MR; r += NLOAD) {
@@ -575,25 +597,43 @@ k_subst_tcp(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ j
 
     if (t < NLOAD) {
         // ------------------------------------------------------------ loaders
+        // the next item is decoded, and the next stage's vector rows looked up, while the
+        // current stage's copies are issued
         long long gs = 0;  // stage counter across this block's items
-        for (long long item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-            const Item it = decode<NT, MODE>(tasks, jobs, item, nchunks, KS);
-            for (int s = 0; s < it.nst && ok; ++s, ++gs) {
+        long long item = blockIdx.x;
+        Item cur;
+        Vrows<NT> rows;
+        if (item < nitems) {
+            cur = decode<NT, MODE>(tasks, jobs, item, nchunks, KS);
+            rows = stage_rows<NT, MODE>(cur, 0, t);
+        }
+        for (; item < nitems && ok; item += gridDim.x) {
+            const long long nxt_item = item + gridDim.x;
+            Item nxt = cur;
+            if (nxt_item < nitems) nxt = decode<NT, MODE>(tasks, jobs, nxt_item, nchunks, KS);
+            for (int s = 0; s < cur.nst && ok; ++s, ++gs) {
                 const int slot = (int)(gs & 1);
                 const long long use = gs >> 1;
+                Vrows<NT> next_rows;
+                if (s + 1 < cur.nst) next_rows = stage_rows<NT, MODE>(cur, s + 1, t);
+                else if (nxt_item < nitems) next_rows = stage_rows<NT, MODE>(nxt, 0, t);
                 if (gs >= 2) ok = mbar_wait(smem_u32(raw_empty + slot), (uint32_t)((use - 1) & 1), abort);
                 if (!ok) break;
-                load_stage<NT, MODE>(raw + slot * RG::RAW, it, s, ldc, t);
+                load_stage<NT, MODE>(raw + slot * RG::RAW, cur, s, ldc, t, rows);
                 cp_async_arrive(raw_full + slot);
+                rows = next_rows;
             }
+            cur = nxt;
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (t < NLOAD + NCONV) {
         // ------------------------------------------------------------ converters
         const int ct = t - NLOAD;
         long long gs = 0;
+        int nst_next = blockIdx.x < nitems ? decode<NT, MODE>(tasks, jobs, blockIdx.x, nchunks, KS).nst : 0;
         for (long long item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-            const int nst = decode<NT, MODE>(tasks, jobs, item, nchunks, KS).nst;
+            const int nst = nst_next;   // decoded one item ahead
+            if (item + gridDim.x < nitems) nst_next = decode<NT, MODE>(tasks, jobs, item + gridDim.x, nchunks, KS).nst;
             for (int s = 0; s < nst && ok; ++s, ++gs) {
                 const int slot = (int)(gs & 1);
                 const long long use = gs >> 1;
@@ -611,8 +651,10 @@ k_subst_tcp(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ j
         if (l == 0) {
             long long gs = 0;
             int nit = 0;  // items of this block so far
+            int nst_next = blockIdx.x < nitems ? decode<NT, MODE>(tasks, jobs, blockIdx.x, nchunks, KS).nst : 0;
             for (long long item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++nit) {
-                const int nst = decode<NT, MODE>(tasks, jobs, item, nchunks, KS).nst;
+                const int nst = nst_next;   // decoded one item ahead
+                if (item + gridDim.x < nitems) nst_next = decode<NT, MODE>(tasks, jobs, item + gridDim.x, nchunks, KS).nst;
                 const int b = nit & 1;
                 if (nit >= 2) ok = mbar_wait(smem_u32(acc_empty + b), (uint32_t)(((nit >> 1) - 1) & 1), abort);
                 if (!ok) break;

@@ -27,7 +27,7 @@ EXPORTED = [
     "hz_default_opts", "hz_create", "hz_factor", "hz_solve", "hz_solve_host", "hz_destroy", "hz_last_error",
     "hz_layer_info", "hz_factor_stats", "hz_layer_solve_cost", "hz_layer_solve", "hz_polarized_rhs",
     "hz_apply_mpol", "hz_apply_precond", "hz_reconstruct", "hz_volume_residual",
-    "hz_profile_begin", "hz_profile_begin_detail", "hz_profile_end", "hz_profile_kernel", "hz_kernel_launches", "hz_volume_residual_noalloc",
+    "hz_profile_begin", "hz_profile_begin_detail", "hz_profile_end", "hz_profile_kernel", "hz_profile_report", "hz_kernel_launches", "hz_volume_residual_noalloc",
     "hz_tuning_report", "hz_solve_group", "hz_create_shared",
 ]
 
@@ -93,13 +93,16 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.hz_profile_kernel.argtypes = [VP, I32, P(ct.c_int64), P(D), P(D), P(D)]
     lib.hz_kernel_launches.argtypes = []
     lib.hz_tuning_report.argtypes = [VP]
+    lib.hz_profile_report.argtypes = [VP]
     lib.hz_create_shared.argtypes = [VP, VP, P(VP)]
     lib.hz_solve_group.argtypes = [P(VP), I32, P(VP), P(I32), P(VP), P(SolveOpts), P(VP), P(ct.c_int)]
     for name in EXPORTED:
-        if name not in ("hz_default_opts", "hz_last_error", "hz_kernel_launches", "hz_tuning_report"):
+        if name not in ("hz_default_opts", "hz_last_error", "hz_kernel_launches", "hz_tuning_report",
+                        "hz_profile_report"):
             getattr(lib, name).restype = ct.c_int
     lib.hz_kernel_launches.restype = ct.c_int64
     lib.hz_tuning_report.restype = ct.c_char_p
+    lib.hz_profile_report.restype = ct.c_char_p
     _lib = lib
     return lib
 
@@ -267,6 +270,10 @@ class Solver:
 
     def tuning_report(self) -> str:
         return self.lib.hz_tuning_report(self.h).decode()
+
+    def profile_report(self) -> str:
+        """Per kernel kind, phase and tree level table of the last detail-profiled interval."""
+        return self.lib.hz_profile_report(self.h).decode()
 
     def profile_begin(self, detail: bool = False):
         fn = self.lib.hz_profile_begin_detail if detail else self.lib.hz_profile_begin
