@@ -8,7 +8,11 @@ handle and CUDA stream; the first worker of a frequency is the factor owner, fur
 they are free, so requests that arrive while other batches are on the GPU join the next batch
 of a free worker, and batches of different frequencies (and of the same frequency, when several
 workers are admitted) run on the device at the same time.  A new worker is admitted only while
-the free device memory covers its estimated workspace for a full batch (admission by free HBM).
+the free device memory, less the estimated workspace of admitted workers that have not yet
+allocated theirs (workspaces are allocated on a worker's first batch), covers its own estimated
+workspace for a full batch (admission by free HBM).  A batch that still runs out of device
+memory is put back at the head of its queue; an extra worker that hit it is retired (its
+workspace freed), and a work item is retried at most twice before its request fails.
 
 All arithmetic runs in the CUDA library; this module only places sources, moves columns in and
 out of batches and keeps time.
@@ -75,6 +79,8 @@ class Server:
         self.batches = 0
         self.max_requests_per_batch = 0
         self.admission_log: List[str] = []
+        self.pending: dict = {}       # id(solver) -> estimated workspace not yet allocated
+        self.retries: dict = {}       # (rid, first column) -> out-of-memory retries so far
 
     # ------------------------------------------------------------------ admission
     def worker_bytes(self, cols: int) -> float:
@@ -99,16 +105,18 @@ class Server:
     def _admit_worker(self, w: int) -> bool:
         if len(self.workers[w]) >= self.max_workers:
             return False
+        need = self.worker_bytes(self.max_cols)
         if self.workers[w]:
             free, _ = self.torch.cuda.mem_get_info()
-            need = self.worker_bytes(self.max_cols)
-            if free - self.mem_reserve < need:
+            pending = sum(self.pending.values())
+            if free - self.mem_reserve - pending < need:
                 self.admission_log.append(f"omega {w}: extra worker refused ({free/1e9:.1f} GB free, "
-                                          f"{need/1e9:.1f} GB needed)")
+                                          f"{pending/1e9:.1f} GB promised, {need/1e9:.1f} GB needed)")
                 return False
             solver = hz.Solver.shared(self.primaries[w])
         else:
             solver = self.primaries[w]
+        self.pending[id(solver)] = need
         self.workers[w].append(solver)
         th = threading.Thread(target=self._work, args=(w, solver), daemon=True)
         self.threads.append(th)
@@ -187,14 +195,48 @@ class Server:
                             req.t_done = now
                     self.cv.notify_all()
             except Exception as e:  # a failed batch marks its requests; the server keeps going
-                with self.cv:
-                    self.errors.append(repr(e))
-                    for req, a, b in items:
-                        req.status = -1
-                        req._left -= (b - a)
-                        if req._left == 0:
-                            req.t_done = time.perf_counter()
-                    self.cv.notify_all()
+                if self._failed_batch(w, solver, items, e):
+                    solver.close()
+                    return
+                continue
+            with self.cv:
+                self.pending.pop(id(solver), None)
+
+    def _failed_batch(self, w: int, solver, items, e: Exception) -> bool:
+        """Bookkeeping of a batch that raised: an out-of-memory batch goes back to the head of its
+        queue (each work item at most twice) and an extra worker that hit it is retired; any other
+        failure, or a third out-of-memory failure, marks the requests failed.  Returns whether the
+        calling worker must retire (its handle is then closed by the caller)."""
+        torch = self.torch
+        oom = (isinstance(e, hz.HzError) and e.status == hz.HZ_ERR_OOM) or \
+            isinstance(e, getattr(getattr(torch, "cuda", None), "OutOfMemoryError", ()))
+        retire = False
+        with self.cv:
+            self.pending.pop(id(solver), None)
+            if oom:
+                retry, failed = [], []
+                for it in items:
+                    key = (it[0].rid, it[1])
+                    self.retries[key] = self.retries.get(key, 0) + 1
+                    (retry if self.retries[key] <= 2 else failed).append(it)
+                for it in reversed(retry):       # back at the head, in their order
+                    self.queues[w].appendleft(it)
+                items = failed
+                retire = solver is not self.primaries[w]
+                if retire:
+                    self.workers[w].remove(solver)
+                    self.admission_log.append(f"omega {w}: worker retired after running out of memory")
+            if items:
+                self.errors.append(repr(e))
+            for req, a, b in items:
+                req.status = -1
+                req._left -= (b - a)
+                if req._left == 0:
+                    req.t_done = time.perf_counter()
+            self.cv.notify_all()
+        if oom and not retire:
+            time.sleep(0.2)   # let retiring workers free their memory before the retry
+        return retire
 
     # ------------------------------------------------------------------ driver
     def serve(self, requests: Sequence[Request], realtime: bool = True, timeout: float = 3600.0):

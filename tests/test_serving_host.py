@@ -1,0 +1,74 @@
+"""Host-side logic of the serving layer (no GPU): admission by free device memory counts the
+workspace promised to admitted workers that have not allocated it yet, and an out-of-memory batch
+is re-queued (at most twice per work item) while the extra worker that hit it retires."""
+import collections
+import threading
+import types
+
+import numpy as np
+
+from paper_1801_08655_gb300 import hz, serving
+
+GB = 1e9
+
+
+class FakeSolver:
+    def __init__(self):
+        self.closed = False
+
+    def close(self):
+        self.closed = True
+
+
+def make_server(free_bytes, need_bytes, monkeypatch):
+    srv = object.__new__(serving.Server)
+    srv.torch = types.SimpleNamespace(cuda=types.SimpleNamespace(mem_get_info=lambda: (free_bytes, 200 * GB)))
+    srv.max_cols, srv.max_workers, srv.mem_reserve = 32, 3, 4 * GB
+    srv.primaries = [FakeSolver()]
+    srv.workers = [[]]
+    srv.queues = [collections.deque()]
+    srv.cv = threading.Condition()
+    srv.threads, srv.errors, srv.admission_log = [], [], []
+    srv.pending, srv.retries = {}, {}
+    srv.running = True
+    srv._work = lambda w, s: None
+    monkeypatch.setattr(serving.Server, "worker_bytes", lambda self, cols: need_bytes)
+    monkeypatch.setattr(serving.hz.Solver, "shared", classmethod(lambda cls, prim: FakeSolver()))
+    return srv
+
+
+def test_admission_counts_promised_workspace(monkeypatch):
+    # room for one workspace beyond the reserve: the primary's (not yet allocated) takes it
+    srv = make_server(free_bytes=4 * GB + 15 * GB, need_bytes=10 * GB, monkeypatch=monkeypatch)
+    assert srv._admit_worker(0)             # primary: always admitted, its workspace promised
+    assert srv.pending and sum(srv.pending.values()) == 10 * GB
+    assert not srv._admit_worker(0)         # 15 GB free - 10 GB promised < 10 GB
+    assert "promised" in srv.admission_log[-1]
+    srv.pending.clear()                     # the primary has allocated (free memory unchanged here)
+    assert srv._admit_worker(0)
+    assert len(srv.workers[0]) == 2
+
+
+def test_out_of_memory_batch_is_requeued_and_extra_worker_retires(monkeypatch):
+    srv = make_server(free_bytes=100 * GB, need_bytes=1 * GB, monkeypatch=monkeypatch)
+    srv._admit_worker(0)
+    srv._admit_worker(0)
+    extra = srv.workers[0][1]
+    req = serving.Request(7, 0, np.zeros((40, 3), dtype=np.int64))
+    req._left = 40
+    items = [(req, 0, 32), (req, 32, 40)]
+    oom = hz.HzError(hz.HZ_ERR_OOM, "device allocation failed")
+    assert srv._failed_batch(0, extra, items, oom) is True       # extra worker retires
+    assert list(srv.queues[0]) == items                          # same order, at the head
+    assert extra not in srv.workers[0] and not srv.errors and req.status == 0
+    prim = srv.primaries[0]
+    srv.queues[0].clear()
+    assert srv._failed_batch(0, prim, items, oom) is False      # second failure: retried again
+    srv.queues[0].clear()
+    assert srv._failed_batch(0, prim, items, oom) is False      # third: the requests fail
+    assert not srv.queues[0] and srv.errors and req.status == -1 and req._left == 0
+    # any other error fails the batch at once
+    req2 = serving.Request(8, 0, np.zeros((3, 3), dtype=np.int64))
+    req2._left = 3
+    assert srv._failed_batch(0, prim, [(req2, 0, 3)], RuntimeError("boom")) is False
+    assert req2.status == -1 and req2.t_done is not None
