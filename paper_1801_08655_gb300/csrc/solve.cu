@@ -10,8 +10,11 @@
 // layers of a batch.  Every block computes a TILE-row slab of one product for a chunk of
 // CC right-hand-side columns over a range of at most KS reduction tiles (split-K keeps the
 // top of the tree, where a level has few nodes with long reductions, spread over the whole
-// GPU); partial products are accumulated with vector atomics into zeroed outputs.  The
-// factor tile stream is the HBM traffic that bounds the kernel at small column counts.
+// GPU).  Outputs are zeroed beforehand; a task covering the whole reduction of its rows stores
+// them, split reductions and FB's update rows (shared between the nodes of a level) accumulate
+// with atomics.  The factor tile stream is the HBM traffic that bounds the kernel at small
+// column counts.  Complex64 blocks of >= 64 columns can instead run on the tensor-core kernels
+// of subst_tc.cu; the autotuner decides per batch signature.
 #include <algorithm>
 
 #include "hz_internal.cuh"
