@@ -474,7 +474,7 @@ def main():
     ap.add_argument("--rhs", type=int, default=0, help="right-hand sides per step (default: the workload's R)")
     ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--rmax", type=int, default=64)
-    ap.add_argument("--max-cols", type=int, default=32)
+    ap.add_argument("--max-cols", type=int, default=64)
     ap.add_argument("--npml-local", type=int, default=5)
     ap.add_argument("--config", type=int, default=3, choices=[2, 3, 4, 5],
                     help="3: 128^3 layered+block, R=128 (the headline workload); 2: 64^3 smooth, R=16; "

@@ -111,6 +111,8 @@ void hz_default_opts(hz_precision prec, hz_solve_opts* opts);
  *                     walking the work items) instead of one block per work item (0)
  *   HZ_AUTOTUNE=0     keep the fixed defaults; HZ_GRAPHS=0 no CUDA-graph replay;
  *   HZ_LEAF           nested-dissection leaf size (cells, default 256)
+ *   HZ_FACTOR_TC_MIN  complex64 fronts with at least this many update unknowns (default 128)
+ *                     compute L21 and their Schur complement on the tensor cores; 0: never
  */
 hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz_pml* pml,
                     int32_t n_layers, hz_precision prec, void* stream, hz_handle** out);
@@ -118,8 +120,10 @@ hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz
 /*
  * hz_factor -- offline phase (Algorithm 1): assemble and factor every layer's
  * local operator H^l = L D L^T (complex symmetric, unpivoted, nested dissection,
- * FP64 diagonal pivot blocks), keeping the factors resident in device memory.
- * Errors: HZ_ERR_OOM, HZ_ERR_PIVOT, HZ_ERR_CUDA.
+ * FP64 diagonal pivot blocks), keeping the factors resident in device memory.  In mixed
+ * precision the L21 and Schur-complement products of large fronts run on the tensor cores
+ * (split-TF32, FP32 accumulation).
+ * Errors: HZ_ERR_OOM, HZ_ERR_PIVOT, HZ_ERR_CUDA, HZ_ERR_TIMEOUT.
  */
 hz_status hz_factor(hz_handle* h);
 
@@ -247,23 +251,41 @@ hz_status hz_volume_residual(hz_handle* h, const double* rhs, const double* u, i
  * ------------------------------------------------------------------------------------ */
 /*
  * hz_volume_residual_noalloc -- the FP64 volume residual of hz_volume_residual computed
- * without allocating any memory during the call.  It has no counterpart in the paper: it
- * exists for callers that cannot allocate device memory where they need the residual (for
- * example while a stream is being captured into a CUDA graph, inside a host callback, or
- * when a caching allocator already owns all free device memory).  The per-column sums
- * the kernel needs live in a fixed device array inside the library instead of a buffer
- * allocated per call; only buffers the handle already owns and the caller's arrays are used.
+ * without allocating any memory during the call.  It has no counterpart in the paper.  It is
+ * for callers that cannot allocate device memory where they need the residual: a process whose
+ * device memory is all held by a caching allocator (a cudaMalloc there fails, or forces the
+ * allocator to release its cache with a device-wide synchronisation), or a serving loop that
+ * must keep a fixed memory footprint per request.  The per-column sums the kernel needs live
+ * in a fixed device array inside the library instead of a buffer allocated per call; only
+ * buffers the handle already owns and the caller's arrays are used.
  *   rhs, u     device complex [R][nz][ny][nx] (f, unscaled; and the candidate solution)
- *   R          1 <= R <= 1024 (the fixed scratch holds 1024 columns); larger R returns
- *              HZ_ERR_ARG with a message saying so
+ *   R          1 <= R <= 1024 (the fixed scratch holds 1024 columns, 16 KiB per device); larger R
+ *              returns HZ_ERR_ARG with a message saying so
  *   r          device complex [R][nz][ny][nx] receiving S f - A u, or NULL
  *   relres_host  host double[R] receiving ||S f - A u|| / ||S f||
- * The first call on a device looks up the device address of the fixed array (set-up); make
- * that first call before any stream capture.  All calls in the process share the array:
- * calls that overlap on the GPU (different streams or threads at once) race on it.
+ * The call runs on the handle's device and stream, copies the sums to the host and
+ * synchronizes that stream before it returns.  The first call on a device looks up the device
+ * address of the fixed array (set-up); make that first call before any stream capture.  All
+ * calls in the process share the array, which keeps the last call's sums (each call clears the
+ * columns it uses): calls that overlap on the GPU (different streams or threads at once) race
+ * on it.
  */
 hz_status hz_volume_residual_noalloc(hz_handle* h, const double* rhs, const double* u, int32_t R, double* r,
                                      double* relres_host);
+
+/*
+ * hz_tensor_peak -- measures the tensor pipe's dense MMA rate on the current device (no
+ * counterpart in the paper; it is the denominator of the tensor-core kernels' roofline).
+ * One block per SM issues tcgen05 MMAs (M = 128, N = n, one instruction's K) from operands
+ * resident in shared memory, with no global-memory traffic, for about `seconds` seconds.
+ *   kind     0: kind::tf32 (tf32 x tf32 -> f32, K = 8); 1: kind::f16 with bf16 operands (K = 16)
+ *   n        64, 128 or 256
+ *   seconds  0 < seconds <= 30
+ *   tflops   receives 2*128*n*K flops per MMA x MMAs / time, in TFLOP/s
+ *   ms       NULL or receives the measured run's device time
+ * Errors: HZ_ERR_ARG, HZ_ERR_OOM, HZ_ERR_CUDA, HZ_ERR_TIMEOUT (the bounded completion wait gave up).
+ */
+hz_status hz_tensor_peak(int32_t kind, int32_t n, double seconds, double* tflops, double* ms);
 
 hz_status hz_profile_begin(hz_handle* h);
 hz_status hz_profile_begin_detail(hz_handle* h);

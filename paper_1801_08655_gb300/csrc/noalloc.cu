@@ -1,13 +1,15 @@
 // Allocation-free variant of the FP64 volume residual (hz_volume_residual_noalloc).
 //
-// Some callers cannot allocate device memory at the point where they need the residual:
-// code that runs while a stream is being captured into a CUDA graph, host callbacks, or
-// processes whose device memory is entirely handed out by a caching allocator (where a
-// cudaMalloc either fails or forces a device-wide synchronisation through cudaFree).  For
-// them this entry point keeps its only scratch -- the per-column partial sums of ||r||^2
-// and ||S f||^2 that the kernel accumulates -- in a fixed file-scope device array instead
-// of a buffer allocated per call.  It reads only buffers the handle already owns (set up
-// by hz_create) and the caller's inputs and outputs.
+// Some callers cannot allocate device memory at the point where they need the residual: a
+// process whose device memory is entirely handed out by a caching allocator (PyTorch's, for
+// example) gets a failed cudaMalloc there, or -- once the allocator releases its cache to make
+// room -- a device-wide synchronisation; a serving loop with a fixed memory budget must not grow
+// its footprint per request.  For them this entry point keeps its only scratch -- the per-column
+// partial sums of ||r||^2 and ||S f||^2 that the kernel accumulates -- in a fixed file-scope
+// device array instead of a buffer allocated per call.  It reads only buffers the handle
+// already owns (set up by hz_create) and the caller's inputs and outputs.  Like the other entry
+// points it returns with the result on the host: it copies the sums to host memory and
+// synchronizes the handle's stream.
 #include <cmath>
 #include <mutex>
 
@@ -28,20 +30,25 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array for the current device.  In host code the array's
-// name is only a host-side stand-in, so the address is looked up once per device (with that
-// device current) and cached.
-hz_status scratch_address(double** out, std::string& err) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        cudaGetLastError();
-        err = "no current CUDA device";
+// Device address of the scratch array on device `dev` (the handle's device).  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once per device, with
+// that device current, and cached; the caller's current device is restored afterwards.
+hz_status scratch_address(int dev, double** out, std::string& err) {
+    if (dev < 0 || dev >= kMaxDevices) {
+        err = "device ordinal out of range";
         return HZ_ERR_CUDA;
     }
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_scratch_addr[dev]) {
+        int prev = 0;
+        if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess) {
+            cudaGetLastError();
+            err = "cannot make the handle's device current";
+            return HZ_ERR_CUDA;
+        }
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_residual_scratch);
+        cudaSetDevice(prev);
         if (e != cudaSuccess || p == nullptr) {
             cudaGetLastError();
             err = std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
@@ -52,6 +59,20 @@ hz_status scratch_address(double** out, std::string& err) {
     *out = g_scratch_addr[dev];
     return HZ_OK;
 }
+
+// Makes `dev` the current device for the lifetime of the guard (the handle's stream and the
+// scratch address belong to it) and restores the caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess) ok = prev == dev || cudaSetDevice(dev) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+    }
+    ~DeviceGuard() {
+        if (ok && prev >= 0) cudaSetDevice(prev);
+    }
+};
 
 // Same arithmetic as the residual kernel of the online path: r = S f - A u with the
 // symmetric-form stretched 7-point operator, plus per-column sums of |r|^2 and |S f|^2.
@@ -126,8 +147,13 @@ extern "C" hz_status hz_volume_residual_noalloc(hz_handle* h, const double* rhs,
                        std::to_string(hz::kNoallocMaxCols) + " columns";
         return HZ_ERR_ARG;
     }
+    hz::DeviceGuard guard(c.device);
+    if (!guard.ok) {
+        c.last_error = "hz_volume_residual_noalloc: cannot make the handle's device current";
+        return HZ_ERR_CUDA;
+    }
     double* scratch = nullptr;
-    hz_status st = hz::scratch_address(&scratch, c.last_error);
+    hz_status st = hz::scratch_address(c.device, &scratch, c.last_error);
     if (st != HZ_OK) return st;
     const long long N3 = (long long)c.nx * c.ny * c.nz;
     // the array keeps the previous call's sums: clear the columns this call accumulates into

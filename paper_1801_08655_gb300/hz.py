@@ -28,7 +28,7 @@ EXPORTED = [
     "hz_layer_info", "hz_factor_stats", "hz_layer_solve_cost", "hz_layer_solve", "hz_polarized_rhs",
     "hz_apply_mpol", "hz_apply_precond", "hz_reconstruct", "hz_volume_residual",
     "hz_profile_begin", "hz_profile_begin_detail", "hz_profile_end", "hz_profile_kernel", "hz_profile_report", "hz_kernel_launches", "hz_volume_residual_noalloc",
-    "hz_tuning_report", "hz_solve_group", "hz_create_shared",
+    "hz_tuning_report", "hz_solve_group", "hz_create_shared", "hz_tensor_peak",
 ]
 
 
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.hz_profile_report.argtypes = [VP]
     lib.hz_create_shared.argtypes = [VP, VP, P(VP)]
     lib.hz_solve_group.argtypes = [P(VP), I32, P(VP), P(I32), P(VP), P(SolveOpts), P(VP), P(ct.c_int)]
+    lib.hz_tensor_peak.argtypes = [I32, I32, D, P(D), P(D)]
     for name in EXPORTED:
         if name not in ("hz_default_opts", "hz_last_error", "hz_kernel_launches", "hz_tuning_report",
                         "hz_profile_report"):
@@ -260,9 +261,23 @@ class Solver:
         self._check(self.lib.hz_reconstruct(self.h, _ptr(rhs), _ptr(t), rhs.shape[0], _ptr(u)))
         return u
 
+    def _check_volume(self, *ts):
+        """Every tensor must be a contiguous complex128 CUDA tensor of shape (R, nz, ny, nx) with
+        the same R (the kernels read R * nz * ny * nx elements of each)."""
+        import torch
+        R = ts[0].shape[0] if ts[0].dim() == 4 else -1
+        for t in ts:
+            if t is None:
+                continue
+            if not (t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()
+                    and tuple(t.shape) == (R,) + self.shape):
+                raise ValueError(f"expected a contiguous complex128 CUDA tensor of shape {(R,) + self.shape}, "
+                                 f"got {tuple(t.shape)} {t.dtype} on {t.device}")
+
     def volume_residual_noalloc(self, rhs, u, r=None):
         """As volume_residual, through the entry point that allocates nothing; r (if given)
         must be a preallocated complex128 CUDA tensor shaped like rhs."""
+        self._check_volume(rhs, u, r)
         R = rhs.shape[0]
         rel = (ct.c_double * R)()
         self._check(self.lib.hz_volume_residual_noalloc(self.h, _ptr(rhs), _ptr(u), R, _ptr(r), rel))
@@ -292,6 +307,7 @@ class Solver:
 
     def volume_residual(self, rhs, u, want_r: bool = False):
         import torch
+        self._check_volume(rhs, u)
         R = rhs.shape[0]
         r = torch.empty_like(rhs) if want_r else None
         rel = (ct.c_double * R)()
@@ -321,6 +337,15 @@ def solve_group(solvers, rhs_list, opts: Optional[SolveOpts] = None, allow_nocon
         bad = [i for i in range(n) if sts[i] not in ok]
         raise HzError(st, f"member {bad[0]}: " + lib.hz_last_error(solvers[bad[0]].h).decode())
     return us, [list(i) for i in infos], list(sts)
+
+
+def tensor_peak(kind: str = "tf32", n: int = 128, seconds: float = 1.0):
+    """Measured dense tcgen05 MMA rate of the current device (hz_tensor_peak): (TFLOP/s, ms)."""
+    tf, ms = ct.c_double(), ct.c_double()
+    st = load().hz_tensor_peak({"tf32": 0, "bf16": 1}[kind], n, seconds, ct.byref(tf), ct.byref(ms))
+    if st != HZ_OK:
+        raise HzError(st, f"hz_tensor_peak({kind}, {n}) failed")
+    return tf.value, ms.value
 
 
 def kernel_launches() -> int:

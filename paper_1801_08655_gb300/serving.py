@@ -39,7 +39,7 @@ class Request:
         self.t_arrival = t_arrival
         self.t_done: Optional[float] = None
         self.result = None          # full solution (R, nz, ny, nx) or receiver samples (R, nrec)
-        self.status = 0
+        self.status = 0             # 0 delivered; -1 failed (a work item raised or did not converge)
         self._left = 0
 
     @property
@@ -53,7 +53,7 @@ class Request:
 
 class Server:
     def __init__(self, m: np.ndarray, omegas: Sequence[float], npml: int, C: float, n_layers: int,
-                 npml_local: int = -1, precision: str = "mixed", max_cols: int = 32, max_workers: int = 2,
+                 npml_local: int = -1, precision: str = "mixed", max_cols: int = 64, max_workers: int = 2,
                  opts: Optional[hz.SolveOpts] = None, receivers: Optional[np.ndarray] = None,
                  mem_reserve_bytes: float = 4e9):
         import torch
@@ -168,7 +168,9 @@ class Server:
                         rhs[k, src[:, 0], src[:, 1], src[:, 2]] = 1.0
                         c += b - a
                 solver.stream.synchronize()
-                u, info, st = solver.solve(rhs, self.opts, allow_noconv=True)
+                # a batch that does not converge raises (HZ_ERR_NO_CONVERGENCE): its requests fail
+                # instead of receiving unconverged columns
+                u, info, st = solver.solve(rhs, self.opts)
                 with torch.cuda.stream(solver.stream):
                     c = 0
                     outs = []
@@ -180,20 +182,7 @@ class Server:
                         outs.append(part.clone())
                         c += b - a
                 solver.stream.synchronize()
-                now = time.perf_counter()
-                with self.cv:
-                    self.batches += 1
-                    self.max_requests_per_batch = max(self.max_requests_per_batch, len({id(r) for r, _, _ in items}))
-                    for (req, a, b), part in zip(items, outs):
-                        if req.result is None:
-                            shp = (req.R,) + tuple(part.shape[1:])
-                            req.result = torch.empty(shp, dtype=part.dtype, device="cuda")
-                        req.result[a:b] = part
-                        req.status = max(req.status, int(st))
-                        req._left -= (b - a)
-                        if req._left == 0:
-                            req.t_done = now
-                    self.cv.notify_all()
+                self._deliver(items, outs, time.perf_counter())
             except Exception as e:  # a failed batch marks its requests; the server keeps going
                 if self._failed_batch(w, solver, items, e):
                     solver.close()
@@ -201,6 +190,24 @@ class Server:
                 continue
             with self.cv:
                 self.pending.pop(id(solver), None)
+
+    def _deliver(self, items, outs, now: float):
+        """Bookkeeping of a solved batch: copy each work item's columns into its request.  A request
+        that already has a failed work item keeps its failure status (-1); it completes when its
+        last work item has been accounted for, failed or delivered."""
+        with self.cv:
+            self.batches += 1
+            self.max_requests_per_batch = max(self.max_requests_per_batch, len({id(r) for r, _, _ in items}))
+            for (req, a, b), part in zip(items, outs):
+                if req.status == 0:
+                    if req.result is None:
+                        shp = (req.R,) + tuple(part.shape[1:])
+                        req.result = self.torch.empty(shp, dtype=part.dtype, device=part.device)
+                    req.result[a:b] = part
+                req._left -= (b - a)
+                if req._left == 0:
+                    req.t_done = now
+            self.cv.notify_all()
 
     def _failed_batch(self, w: int, solver, items, e: Exception) -> bool:
         """Bookkeeping of a batch that raised: an out-of-memory batch goes back to the head of its
@@ -230,6 +237,7 @@ class Server:
                 self.errors.append(repr(e))
             for req, a, b in items:
                 req.status = -1
+                req.result = None           # a failed request delivers no partial result
                 req._left -= (b - a)
                 if req._left == 0:
                     req.t_done = time.perf_counter()

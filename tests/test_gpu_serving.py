@@ -27,7 +27,7 @@ def test_served_results_equal_standalone_solves():
         reqs.append(serving.Request(i, int(rng.integers(0, 2)), src, t_arrival=0.01 * i))
     wall = srv.serve(reqs)
     assert not srv.errors, srv.errors
-    assert all(r.t_done is not None and r.status in (0, 7) for r in reqs)
+    assert all(r.t_done is not None and r.status == 0 for r in reqs)
     assert srv.max_requests_per_batch >= 2          # requests were batched together
     st = serving.latency_stats(reqs)
     assert 0 < st["p50_s"] <= st["p99_s"] <= wall + 1e-6

@@ -72,3 +72,24 @@ def test_out_of_memory_batch_is_requeued_and_extra_worker_retires(monkeypatch):
     req2._left = 3
     assert srv._failed_batch(0, prim, [(req2, 0, 3)], RuntimeError("boom")) is False
     assert req2.status == -1 and req2.t_done is not None
+
+
+def test_failed_item_keeps_request_failed_when_a_later_item_succeeds(monkeypatch):
+    srv = make_server(free_bytes=100 * GB, need_bytes=1 * GB, monkeypatch=monkeypatch)
+    srv.batches, srv.max_requests_per_batch = 0, 0
+    srv.torch = types.SimpleNamespace(empty=lambda shp, dtype=None, device=None: np.zeros(shp, dtype=dtype),
+                                      cuda=srv.torch.cuda)
+    srv._admit_worker(0)
+    prim = srv.primaries[0]
+    req = serving.Request(9, 0, np.zeros((40, 3), dtype=np.int64))
+    req._left = 40
+    noconv = hz.HzError(hz.HZ_ERR_NO_CONVERGENCE, "GMRES hit its iteration cap")
+    assert srv._failed_batch(0, prim, [(req, 0, 32)], noconv) is False
+    assert req.status == -1 and req.t_done is None and req._left == 8
+    srv._deliver([(req, 32, 40)], [np.ones((8, 5), dtype=np.complex128)], now=1.0)
+    assert req.status == -1 and req.result is None and req.t_done == 1.0 and req._left == 0
+    # a request whose items all succeed is delivered whole
+    ok = serving.Request(10, 0, np.zeros((3, 3), dtype=np.int64))
+    ok._left = 3
+    srv._deliver([(ok, 0, 2), (ok, 2, 3)], [np.full((2, 5), 1.0 + 0j), np.full((1, 5), 2.0 + 0j)], now=2.0)
+    assert ok.status == 0 and ok.t_done == 2.0 and ok.result.shape == (3, 5) and ok.result[2, 0] == 2.0
