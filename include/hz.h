@@ -111,6 +111,7 @@ void hz_default_opts(hz_precision prec, hz_solve_opts* opts);
  *                     walking the work items) instead of one block per work item (0)
  *   HZ_AUTOTUNE=0     keep the fixed defaults; HZ_GRAPHS=0 no CUDA-graph replay;
  *   HZ_LEAF           nested-dissection leaf size (cells, default 256)
+ *   HZ_FACTOR_PROFILE=1  time every factorization launch by kernel kind (hz_factor_report)
  *   HZ_FACTOR_TC_MIN  complex64 fronts with at least this many update unknowns (default 128)
  *                     compute L21 and their Schur complement on the tensor cores; 0: never
  */
@@ -299,6 +300,12 @@ int64_t hz_kernel_launches(void);
  * work items (tasks, before the split into column chunks), summed device ms and algorithmic
  * TFLOP/s.  The string stays valid until the next call on the handle. */
 const char* hz_profile_report(hz_handle* h);
+
+/* Per-kernel-kind device time of the last hz_factor on this handle (one line per kind: launch
+ * groups timed and summed ms), recorded only when the environment variable HZ_FACTOR_PROFILE=1
+ * was set at hz_create ("" otherwise; the event pairs serialise nothing but add host work).  The
+ * string stays valid until the next hz_factor on the handle. */
+const char* hz_factor_report(hz_handle* h);
 
 /* The substitution autotuner's record for this handle: one line per tuned batch signature
  * (layer shapes and column width) with the time of every candidate split-K depth and column

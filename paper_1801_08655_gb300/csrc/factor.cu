@@ -29,6 +29,9 @@ template <class C> struct FrontDesc {
     const AsmEntry* ent;  // this node's assembly entries
     long long linv_off, l21_off;
     int m, nown, nupd, own0, nasm, layer;
+    int lim;              // rows/columns the panel steps update: m, or nown when the L21 and Schur
+                          // products run on the tensor cores afterwards (factor_tc.cu)
+    int tc;               // 1: L21 and the Schur update come from the tensor-core products
 };
 
 template <class C> struct ExtDesc {
@@ -158,7 +161,7 @@ __global__ void k_panel(const FrontDesc<C>* fd, int k0) {
     if (k0 >= f.nown) return;
     const int nb = min(TILE, f.nown - k0);
     const int r0 = k0 + nb + blockIdx.x * TILE;
-    if (r0 >= f.m) return;
+    if (r0 >= f.lim) return;
     __shared__ C A[TILE][TILE + 1];   // A[k][r]
     __shared__ C X[TILE][TILE + 1];   // X[k][c] = Linv_kk[c][k]
     __shared__ C Di[TILE];
@@ -168,7 +171,7 @@ __global__ void k_panel(const FrontDesc<C>* fd, int k0) {
     for (int q = t; q < TILE2; q += blockDim.x) {
         int r = q % TILE, k = q / TILE;
         C v = czero<C>();
-        if (r0 + r < f.m && k < nb) v = f.F[(long long)(r0 + r) + (long long)(k0 + k) * f.m];
+        if (r0 + r < f.lim && k < nb) v = f.F[(long long)(r0 + r) + (long long)(k0 + k) * f.m];
         A[k][r] = v;
         // tile is column-major: element (row=c, col=k) at c + k*TILE
         int c = q % TILE, kk = q / TILE;
@@ -186,7 +189,7 @@ __global__ void k_panel(const FrontDesc<C>* fd, int k0) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) cfma(acc[u], av, X[k][cg * 4 + u]);
     }
-    if (r0 + r < f.m) {
+    if (r0 + r < f.lim) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             int c = cg * 4 + u;
@@ -197,14 +200,14 @@ __global__ void k_panel(const FrontDesc<C>* fd, int k0) {
 }
 
 // Trailing update of the lower triangle: F[i, j] -= sum_k L[i,k] D[k] L[j,k] for
-// k0+nb <= j <= i < m, one TILE x TILE output tile per block.
+// k0+nb <= j <= i < lim, one TILE x TILE output tile per block.
 template <class C>
 __global__ void k_update(const FrontDesc<C>* fd, int k0) {
     const FrontDesc<C>& f = fd[blockIdx.y];
     if (k0 >= f.nown) return;
     const int nb = min(TILE, f.nown - k0);
     const int s = k0 + nb;
-    const int T = cdiv_dev(f.m - s, TILE);
+    const int T = cdiv_dev(f.lim - s, TILE);
     const long long q = blockIdx.x;
     if (T <= 0 || q >= (long long)T * (T + 1) / 2) return;
     int ti = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
@@ -220,8 +223,8 @@ __global__ void k_update(const FrontDesc<C>* fd, int k0) {
         C vi = czero<C>(), vj = czero<C>();
         if (k < nb) {
             long long col = (long long)(k0 + k) * f.m;
-            if (i0 + r < f.m) vi = f.F[(i0 + r) + col];
-            if (j0 + r < f.m) vj = cmul(f.F[(j0 + r) + col], f.F[(long long)(k0 + k) + col]);
+            if (i0 + r < f.lim) vi = f.F[(i0 + r) + col];
+            if (j0 + r < f.lim) vj = cmul(f.F[(j0 + r) + col], f.F[(long long)(k0 + k) + col]);
         }
         Li[k][r] = vi;
         Lj[k][r] = vj;
@@ -237,11 +240,11 @@ __global__ void k_update(const FrontDesc<C>* fd, int k0) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) cfma(acc[u], av, Lj[k][cg * 4 + u]);
     }
-    if (i0 + r < f.m) {
+    if (i0 + r < f.lim) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             int c = j0 + cg * 4 + u;
-            if (c < f.m && c <= i0 + r) {
+            if (c < f.lim && c <= i0 + r) {
                 long long idx = (long long)(i0 + r) + (long long)c * f.m;
                 f.F[idx] = csub(f.F[idx], acc[u]);
             }
@@ -304,6 +307,7 @@ __global__ void k_inverse_row(const FrontDesc<C>* fd, int i) {
 template <class C>
 __global__ void k_pack_l21(const FrontDesc<C>* fd) {
     const FrontDesc<C>& f = fd[blockIdx.y];
+    if (f.tc) return;   // written by the tensor-core L21 product
     const int own_t = cdiv_dev(f.nown, TILE), upd_t = cdiv_dev(f.nupd, TILE);
     const int q = blockIdx.x;
     if (q >= own_t * upd_t) return;
@@ -320,9 +324,33 @@ __global__ void k_pack_l21(const FrontDesc<C>* fd) {
 
 }  // namespace
 
+// Kernel kinds of the factorization, for the optional per-kind timing (HZ_FACTOR_PROFILE=1).
+enum { FK_ASSEMBLE, FK_EXTEND, FK_DIAG, FK_PANEL, FK_UPDATE, FK_INVERSE, FK_GEMM_L21, FK_GEMM_SCHUR, FK_PACK, FK_N };
+const char* const kFactorKindNames[FK_N] = {"k_assemble", "k_extend_add", "k_diag", "k_panel", "k_update",
+                                            "k_inverse_row", "k_front_gemm L21", "k_front_gemm Schur", "k_pack_l21"};
+
 template <class C>
 void factor_layers(Ctx& ctx) {
     cudaStream_t st = ctx.stream;
+    // per-kind launch timing: an event pair around every launch, read after the factorization
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> fprof;
+    cudaEvent_t fp_e0 = nullptr;
+#define FP_BEGIN()                                                            \
+    do {                                                                      \
+        if (ctx.factor_prof) {                                                \
+            HZ_CUDA(cudaEventCreate(&fp_e0));                                 \
+            HZ_CUDA(cudaEventRecord(fp_e0, st));                              \
+        }                                                                     \
+    } while (0)
+#define FP_END(kind)                                                          \
+    do {                                                                      \
+        if (ctx.factor_prof) {                                                \
+            cudaEvent_t e1_;                                                  \
+            HZ_CUDA(cudaEventCreate(&e1_));                                   \
+            HZ_CUDA(cudaEventRecord(e1_, st));                                \
+            fprof.push_back({(kind), {fp_e0, e1_}});                          \
+        }                                                                     \
+    } while (0)
     const int L = (int)ctx.layers.size();
     // front arena: as many layers per group as the budget allows
     long long max_front = 0;
@@ -349,6 +377,11 @@ void factor_layers(Ctx& ctx) {
     FrontDesc<C>* d_fd = nullptr;
     ExtDesc<C>* d_ed = nullptr;
     size_t fd_cap = 0, ed_cap = 0;
+    void* d_gd = nullptr;
+    void* d_gi = nullptr;
+    size_t gd_cap = 0, gi_cap = 0;
+    // the L21 and Schur products of large complex64 fronts run on the tensor cores
+    const bool use_tc = sizeof(C) == 8 && ctx.factor_tc_min_upd > 0;
     try {
         for (int g0 = 0; g0 < L; g0 += G) {
             const int g1 = std::min(L, g0 + G);
@@ -358,6 +391,7 @@ void factor_layers(Ctx& ctx) {
                 Hmax = std::max(Hmax, (int)ctx.shapes[ctx.layers[l].shape].levels.size());
             for (int h = 0; h < Hmax; ++h) {
                 std::vector<FrontDesc<C>> fds;
+                std::vector<FrontGemmDesc> gds;
                 std::vector<ExtDesc<C>> eds[2];
                 int max_nasm = 0, max_own = 0, max_rt = 0, max_tri = 0, max_pack = 0, max_ext = 0;
                 for (int l = g0; l < g1; ++l) {
@@ -376,14 +410,27 @@ void factor_layers(Ctx& ctx) {
                         f.ent = sh.d_asm + nd.asm_off;
                         f.m = nd.m; f.nown = nd.nown; f.nupd = nd.nupd; f.own0 = nd.own0;
                         f.nasm = nd.nasm; f.layer = l;
+                        f.tc = (use_tc && front_gemm_eligible(nd.nown, nd.nupd, ctx.factor_tc_min_upd)) ? 1 : 0;
+                        f.lim = f.tc ? nd.nown : nd.m;
                         fds.push_back(f);
+                        if (f.tc) {
+                            FrontGemmDesc g;
+                            g.F = (float2*)f.F;
+                            g.fac = (float2*)f.fac;
+                            g.dinv = (const float2*)f.dinv;
+                            g.linv_off = nd.linv_off;
+                            g.l21_off = nd.l21_off;
+                            g.m = nd.m; g.nown = nd.nown; g.nupd = nd.nupd; g.own0 = nd.own0;
+                            g.own_t = nd.own_t; g.upd_t = nd.upd_t;
+                            gds.push_back(g);
+                        }
                         max_nasm = std::max(max_nasm, nd.nasm);
                         max_own = std::max(max_own, nd.nown);
-                        int rows = nd.m - std::min(nd.nown, TILE);
+                        int rows = f.lim - std::min(nd.nown, TILE);
                         max_rt = std::max(max_rt, cdiv(std::max(rows, 0), TILE));
-                        int T = cdiv(nd.m - std::min(nd.nown, TILE), TILE);
+                        int T = cdiv(std::max(rows, 0), TILE);
                         max_tri = std::max(max_tri, T * (T + 1) / 2);
-                        max_pack = std::max(max_pack, nd.own_t * nd.upd_t);
+                        if (!f.tc) max_pack = std::max(max_pack, nd.own_t * nd.upd_t);
                         for (int k = 0; k < nd.nchild; ++k) {
                             const Node& ch = sh.nodes[nd.child[k]];
                             ExtDesc<C> e;
@@ -407,8 +454,10 @@ void factor_layers(Ctx& ctx) {
                                         cudaMemcpyHostToDevice, st));
                 // 1. original entries
                 if (max_nasm > 0) {
+                    FP_BEGIN();
                     k_assemble<C><<<dim3(cdiv(max_nasm, 256), nf), 256, 0, st>>>(d_fd, ctx.d_coefs);
                     HZ_CHECK_LAUNCH();
+                    FP_END(FK_ASSEMBLE);
                 }
                 // 2. extend-add, one child slot at a time (siblings overlap in the parent)
                 {
@@ -426,37 +475,82 @@ void factor_layers(Ctx& ctx) {
                     long long work = (long long)max_ext * max_ext;
                     int gx = (int)std::min<long long>(4096, std::max<long long>(1, (work + 255) / 256));
                     if (n0) {
+                        FP_BEGIN();
                         k_extend_add<C><<<dim3(gx, (unsigned)n0), 256, 0, st>>>(d_ed);
                         HZ_CHECK_LAUNCH();
+                        FP_END(FK_EXTEND);
                     }
                     if (n1) {
+                        FP_BEGIN();
                         k_extend_add<C><<<dim3(gx, (unsigned)n1), 256, 0, st>>>(d_ed + n0);
                         HZ_CHECK_LAUNCH();
+                        FP_END(FK_EXTEND);
                     }
                 }
                 // 3. blocked partial LDL^T
                 for (int k0 = 0; k0 < max_own; k0 += TILE) {
+                    FP_BEGIN();
                     k_diag<C><<<nf, 256, 0, st>>>(d_fd, k0, ctx.d_flag);
                     HZ_CHECK_LAUNCH();
+                    FP_END(FK_DIAG);
                     if (max_rt > 0) {
+                        FP_BEGIN();
                         k_panel<C><<<dim3(max_rt, nf), 256, 0, st>>>(d_fd, k0);
                         HZ_CHECK_LAUNCH();
+                        FP_END(FK_PANEL);
                     }
                     if (max_tri > 0) {
+                        FP_BEGIN();
                         k_update<C><<<dim3(max_tri, nf), 256, 0, st>>>(d_fd, k0);
                         HZ_CHECK_LAUNCH();
+                        FP_END(FK_UPDATE);
                     }
                 }
                 // 4. selective inversion of L11
                 const int max_own_t = cdiv(max_own, TILE);
                 for (int i = 1; i < max_own_t; ++i) {
+                    FP_BEGIN();
                     k_inverse_row<C><<<dim3(i, nf), 256, 0, st>>>(d_fd, i);
                     HZ_CHECK_LAUNCH();
+                    FP_END(FK_INVERSE);
                 }
-                // 5. pack L21
+                // 5. tensor-core fronts: L21 = F21 L11^{-T} D^{-1} into the packed tiles, then the
+                //    Schur complement F22 -= L21 D L21^T
+                if (!gds.empty()) {
+                    std::vector<GemmItem> it_l21, it_schur;
+                    front_gemm_items(gds, it_l21, it_schur);
+                    const size_t need_g = gds.size() * sizeof(FrontGemmDesc);
+                    const size_t need_i = (it_l21.size() + it_schur.size()) * sizeof(GemmItem);
+                    if (need_g > gd_cap) {
+                        if (d_gd) cudaFree(d_gd);
+                        gd_cap = need_g * 2;
+                        HZ_CUDA(cudaMalloc(&d_gd, gd_cap));
+                    }
+                    if (need_i > gi_cap) {
+                        if (d_gi) cudaFree(d_gi);
+                        gi_cap = need_i * 2;
+                        HZ_CUDA(cudaMalloc(&d_gi, gi_cap));
+                    }
+                    HZ_CUDA(cudaMemcpyAsync(d_gd, gds.data(), need_g, cudaMemcpyHostToDevice, st));
+                    GemmItem* d_items = (GemmItem*)d_gi;
+                    HZ_CUDA(cudaMemcpyAsync(d_items, it_l21.data(), it_l21.size() * sizeof(GemmItem),
+                                            cudaMemcpyHostToDevice, st));
+                    HZ_CUDA(cudaMemcpyAsync(d_items + it_l21.size(), it_schur.data(), it_schur.size() * sizeof(GemmItem),
+                                            cudaMemcpyHostToDevice, st));
+                    FP_BEGIN();
+                    launch_front_gemm(0, d_items, (long long)it_l21.size(), (const FrontGemmDesc*)d_gd, ctx.d_flag + 1, st);
+                    FP_END(FK_GEMM_L21);
+                    FP_BEGIN();
+                    launch_front_gemm(1, d_items + it_l21.size(), (long long)it_schur.size(), (const FrontGemmDesc*)d_gd,
+                                      ctx.d_flag + 1, st);
+                    FP_END(FK_GEMM_SCHUR);
+                }
+                // 6. pack L21 (fronts factored by the panel steps alone)
                 if (max_pack > 0) {
+                    FP_BEGIN();
                     k_pack_l21<C><<<dim3(max_pack, nf), 256, 0, st>>>(d_fd);
                     HZ_CHECK_LAUNCH();
+                    FP_END(FK_PACK);
                 }
                 HZ_CUDA(cudaStreamSynchronize(st));
             }
@@ -465,12 +559,33 @@ void factor_layers(Ctx& ctx) {
         cudaFree(arena);
         if (d_fd) cudaFree(d_fd);
         if (d_ed) cudaFree(d_ed);
+        if (d_gd) cudaFree(d_gd);
+        if (d_gi) cudaFree(d_gi);
         throw;
     }
     HZ_CUDA(cudaStreamSynchronize(st));
     cudaFree(arena);
     if (d_fd) cudaFree(d_fd);
     if (d_ed) cudaFree(d_ed);
+    if (d_gd) cudaFree(d_gd);
+    if (d_gi) cudaFree(d_gi);
+    if (ctx.factor_prof) {
+        double ms[FK_N] = {};
+        long long n[FK_N] = {};
+        for (auto& r : fprof) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, r.second.first, r.second.second);
+            ms[r.first] += t;
+            n[r.first] += 1;
+            cudaEventDestroy(r.second.first);
+            cudaEventDestroy(r.second.second);
+        }
+        ctx.factor_text = "kernel launch_groups ms\n";
+        for (int k = 0; k < FK_N; ++k)
+            ctx.factor_text += std::string(kFactorKindNames[k]) + " " + std::to_string(n[k]) + " " + std::to_string(ms[k]) + "\n";
+    }
+#undef FP_BEGIN
+#undef FP_END
 }
 
 template void factor_layers<float2>(Ctx&);

@@ -422,6 +422,8 @@ hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz
         // HZ_PRECOND_SPLIT=1: single-term TF32 tensor-core products inside the preconditioner
         if (const char* e = std::getenv("HZ_PRECOND_SPLIT")) c.precond_split = std::atoi(e) == 1 ? 1 : 3;
         if (const char* e = std::getenv("HZ_TC_CFG")) c.tc_cfg = std::atoi(e) == 0 ? 0 : 1;
+        if (const char* e = std::getenv("HZ_FACTOR_TC_MIN")) c.factor_tc_min_upd = std::max(0, std::atoi(e));
+        if (const char* e = std::getenv("HZ_FACTOR_PROFILE")) c.factor_prof = std::atoi(e) != 0;
         HZ_CUDA(cudaDeviceSynchronize());  // uploads complete before any work on the stream
         *out = h;
         return HZ_OK;
@@ -463,6 +465,10 @@ hz_status hz_factor(hz_handle* h) {
         cudaEventDestroy(e1);
         int flag[4];
         d2h(c, flag, c.d_flag, sizeof(flag));
+        if (flag[1]) {
+            HZ_CUDA(cudaMemset(c.d_flag + 1, 0, sizeof(int)));
+            throw Error{HZ_ERR_TIMEOUT, "a tensor-core factorization block gave up waiting on its MMAs"};
+        }
         if (flag[0]) throw Error{HZ_ERR_PIVOT, "tiny or non-finite pivot in the unpivoted LDL^T"};
         c.factored = true;
         return HZ_OK;
@@ -830,6 +836,11 @@ hz_status hz_solve_group(hz_handle* const* hs, int32_t n, const double* const* r
         if (worst == HZ_OK && st[i] != HZ_OK) worst = st[i];
     }
     return worst;
+}
+
+const char* hz_factor_report(hz_handle* h) {
+    if (!h) return "";
+    return h->ctx.factor_text.c_str();
 }
 
 const char* hz_profile_report(hz_handle* h) {

@@ -182,6 +182,11 @@ struct Ctx {
     int tc_min_tiles = 8;   // output tiles a node product needs to run on the tensor cores
     int tc_cfg = 0;         // untuned tensor-core kernel: 0 one block per work item, 1 persistent (HZ_TC_CFG)
     int precond_split = 3;  // TF32 terms of the tensor-core products inside the preconditioner (3 or 1)
+    bool factor_prof = false;     // time every factorization launch by kernel kind (HZ_FACTOR_PROFILE=1)
+    std::string factor_text;      // per-kind table of the last profiled factorization
+    int factor_tc_min_upd = 128;  // complex64 fronts with at least this many update unknowns (and a
+                                  // full tile of own unknowns) get their L21 and Schur products on
+                                  // the tensor cores; 0 switches this off (HZ_FACTOR_TC_MIN)
     std::vector<ProfRec> prof_recs;
     bool prof_detail = false;                 // also time every substitution launch by kernel kind
     std::vector<ProfRec> prof_launch;
@@ -191,6 +196,22 @@ struct Ctx {
 };
 
 template <class C> void factor_layers(Ctx& ctx);
+
+// Tensor-core products of the factorization of complex64 fronts (factor_tc.cu): L21 = F21 L11^{-T}
+// D^{-1} into the packed factor tiles, then F22 -= L21 D L21^T in the front.
+struct FrontGemmDesc {
+    float2* F;             // dense front (m x m, column-major)
+    float2* fac;           // layer's packed factor tiles
+    const float2* dinv;    // layer's D^{-1} by elimination index
+    long long linv_off, l21_off;
+    int m, nown, nupd, own0, own_t, upd_t;
+};
+struct GemmItem { int front, ti, tj, nst; };   // 128 x 128 output tile (ti, tj), pipeline stages
+bool front_gemm_eligible(int nown, int nupd, int min_upd);
+void front_gemm_items(const std::vector<FrontGemmDesc>& fronts, std::vector<GemmItem>& l21,
+                      std::vector<GemmItem>& schur);
+void launch_front_gemm(int mode, const GemmItem* d_items, long long n, const FrontGemmDesc* d_fronts, int* flag,
+                       cudaStream_t st);
 
 }  // namespace hz
 

@@ -42,106 +42,15 @@
 #include "hz_internal.cuh"
 #include "hz_ctx.cuh"
 #include "hz_solve.cuh"
+#include "tc_common.cuh"
 
 namespace hz {
 
 namespace {
 
+using namespace tcc;
+
 enum { FA = 0, FB = 1, BA = 2, BB = 3 };
-
-constexpr int KC = 16;                 // complex reduction indices per stage
-constexpr int LBO = 128;               // bytes between core matrices along K
-constexpr int SBO = (KC / 4) * 128;    // bytes between 8-row groups (K = 16 tf32 per row)
-constexpr int MR = 128;                // complex output rows per work item (4 tiles)
-constexpr int TROW = KC * 8 + 16;      // padded raw row (transposed tiles): 144 bytes
-constexpr long long WAIT_LIMIT = 1LL << 26;            // polls of one mbarrier wait at most ...
-constexpr unsigned long long WAIT_NS = 2000000000ull;  // ... and at most 2 s of wall time
-constexpr int NLOAD = 128, NCONV = 256;                // loader and converter threads
-
-__device__ inline long long tri_idx(int rt, int ct) { return (long long)rt * (rt + 1) / 2 + ct; }
-
-__device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ inline uint64_t smem_desc(uint32_t saddr) {
-    uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
-    d |= (uint64_t)(LBO >> 4) << 16;
-    d |= (uint64_t)(SBO >> 4) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version; base offset 0; no swizzle
-    return d;
-}
-
-// byte offset of (row, k) in a [rows x KC] K-major core-matrix operand (4-byte elements)
-__device__ inline int coff(int row, int k) { return (row >> 3) * SBO + (k >> 2) * LBO + (row & 7) * 16 + (k & 3) * 4; }
-
-__device__ inline float tf32_hi(float v) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-    return __uint_as_float(r);
-}
-
-// 16-byte asynchronous global->shared copy; src_bytes = 0 zero-fills without reading
-__device__ inline void cp16(uint32_t dst, const void* src, int src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-
-__device__ inline unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Bounded wait for the phase of the given parity: gives up (false) after WAIT_LIMIT polls,
-// WAIT_NS of wall time, or as soon as another role of the block has raised *abort.
-__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
-    unsigned long long t0 = 0;
-    for (long long it = 0; it < WAIT_LIMIT; ++it) {
-        uint32_t ok;
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-                     : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-        if (ok) return true;
-        if ((it & 255) == 255) {
-            if (*abort) return false;
-            const unsigned long long now = global_ns();
-            if (t0 == 0) t0 = now;
-            else if (now - t0 > WAIT_NS) break;
-        }
-    }
-    *abort = 1;
-    return false;
-}
-
-__device__ inline void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-                 :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ inline void mbar_init(uint64_t* b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(b)), "r"(count));
-}
-__device__ inline void mbar_arrive(uint64_t* b) {
-    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" :: "r"(smem_u32(b)) : "memory");
-}
-// arrive on b once all of this thread's earlier cp.async copies have landed
-__device__ inline void cp_async_arrive(uint64_t* b) {
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" :: "r"(smem_u32(b)) : "memory");
-}
-__device__ inline void mma_commit(uint64_t* b) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(smem_u32(b)));
-}
-
-// 16 consecutive accumulator columns of this warp's 32 TMEM lanes (real and imaginary part)
-__device__ inline void tmem_ld16(uint32_t ar, uint32_t ai, uint32_t (&vr)[16], uint32_t (&vi)[16]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                 : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]), "=r"(vr[7]),
-                   "=r"(vr[8]), "=r"(vr[9]), "=r"(vr[10]), "=r"(vr[11]), "=r"(vr[12]), "=r"(vr[13]), "=r"(vr[14]), "=r"(vr[15])
-                 : "r"(ar));
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                 : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]), "=r"(vi[7]),
-                   "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]), "=r"(vi[13]), "=r"(vi[14]), "=r"(vi[15])
-                 : "r"(ai));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
 // Sizes of one ring stage for NT columns.
 template <int NT> struct Ring {
@@ -293,38 +202,6 @@ __device__ inline void convert_stage(const unsigned char* rb, unsigned char* cv,
         if (SPLIT == 3) {
             *(float4*)(cv + off + 1 * RG::X_MAT) = make_float4(re[0] - rh.x, re[1] - rh.y, re[2] - rh.z, re[3] - rh.w);
             *(float4*)(cv + off + 3 * RG::X_MAT) = make_float4(im[0] - ih.x, im[1] - ih.y, im[2] - ih.z, im[3] - ih.w);
-        }
-    }
-}
-
-// MMA part of a stage (one thread): 2 x (4 or 12) MMAs of 8 complex reduction indices.
-template <int NT, int SPLIT>
-__device__ inline void mma_stage(uint32_t base, uint32_t tm_r, uint32_t tm_i, bool first_stage) {
-    using RG = Ring<NT>;
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(MR >> 4) << 24);
-    const uint32_t idesc_neg = idesc | (1u << 13);
-#pragma unroll
-    for (int ks = 0; ks < KC / 8; ++ks) {
-        const uint32_t ko = ks * 2 * LBO;
-        const uint64_t arh = smem_desc(base + 0 * RG::A_MAT + ko), arl = smem_desc(base + 1 * RG::A_MAT + ko);
-        const uint64_t aih = smem_desc(base + 2 * RG::A_MAT + ko), ail = smem_desc(base + 3 * RG::A_MAT + ko);
-        const uint32_t xb = base + 4 * RG::A_MAT + ko;
-        const uint64_t xrh = smem_desc(xb), xrl = smem_desc(xb + RG::X_MAT);
-        const uint64_t xih = smem_desc(xb + 2 * RG::X_MAT), xil = smem_desc(xb + 3 * RG::X_MAT);
-        const uint32_t first = (first_stage && ks == 0) ? 0u : 1u;
-        mma_tf32(tm_r, arh, xrh, idesc, first);      // Yr = Ar Xr - Ai Xi
-        mma_tf32(tm_r, aih, xih, idesc_neg, 1u);
-        mma_tf32(tm_i, aih, xrh, idesc, first);      // Yi = Ai Xr + Ar Xi
-        mma_tf32(tm_i, arh, xih, idesc, 1u);
-        if (SPLIT == 3) {                             // hi x lo and lo x hi terms
-            mma_tf32(tm_r, arh, xrl, idesc, 1u);
-            mma_tf32(tm_r, arl, xrh, idesc, 1u);
-            mma_tf32(tm_r, aih, xil, idesc_neg, 1u);
-            mma_tf32(tm_r, ail, xih, idesc_neg, 1u);
-            mma_tf32(tm_i, aih, xrl, idesc, 1u);
-            mma_tf32(tm_i, ail, xrh, idesc, 1u);
-            mma_tf32(tm_i, arh, xil, idesc, 1u);
-            mma_tf32(tm_i, arl, xih, idesc, 1u);
         }
     }
 }

@@ -28,7 +28,7 @@ EXPORTED = [
     "hz_layer_info", "hz_factor_stats", "hz_layer_solve_cost", "hz_layer_solve", "hz_polarized_rhs",
     "hz_apply_mpol", "hz_apply_precond", "hz_reconstruct", "hz_volume_residual",
     "hz_profile_begin", "hz_profile_begin_detail", "hz_profile_end", "hz_profile_kernel", "hz_profile_report", "hz_kernel_launches", "hz_volume_residual_noalloc",
-    "hz_tuning_report", "hz_solve_group", "hz_create_shared", "hz_tensor_peak",
+    "hz_tuning_report", "hz_solve_group", "hz_create_shared", "hz_tensor_peak", "hz_factor_report",
 ]
 
 
@@ -97,9 +97,11 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.hz_create_shared.argtypes = [VP, VP, P(VP)]
     lib.hz_solve_group.argtypes = [P(VP), I32, P(VP), P(I32), P(VP), P(SolveOpts), P(VP), P(ct.c_int)]
     lib.hz_tensor_peak.argtypes = [I32, I32, D, P(D), P(D)]
+    lib.hz_factor_report.argtypes = [VP]
+    lib.hz_factor_report.restype = ct.c_char_p
     for name in EXPORTED:
         if name not in ("hz_default_opts", "hz_last_error", "hz_kernel_launches", "hz_tuning_report",
-                        "hz_profile_report"):
+                        "hz_profile_report", "hz_factor_report"):
             getattr(lib, name).restype = ct.c_int
     lib.hz_kernel_launches.restype = ct.c_int64
     lib.hz_tuning_report.restype = ct.c_char_p
@@ -282,6 +284,10 @@ class Solver:
         rel = (ct.c_double * R)()
         self._check(self.lib.hz_volume_residual_noalloc(self.h, _ptr(rhs), _ptr(u), R, _ptr(r), rel))
         return list(rel)
+
+    def factor_report(self) -> str:
+        """Per-kernel-kind device time of the last factorization (HZ_FACTOR_PROFILE=1 at creation)."""
+        return self.lib.hz_factor_report(self.h).decode()
 
     def tuning_report(self) -> str:
         return self.lib.hz_tuning_report(self.h).decode()

@@ -421,3 +421,37 @@ def test_group_solve_matches_individual_solves(hz):
         assert rel(us[k].cpu().numpy(), refs[k]) < E2E_TOL["mixed"]
         assert sts[k] == 0
         s.close()
+
+
+@pytest.mark.parametrize("min_upd", ["32", "0"])
+def test_tensor_core_factorization_layer_solve(hz, min_upd, monkeypatch):
+    """Local solves of a layer factored with the tensor-core L21 and Schur products on every front
+    with >= 32 update unknowns (min_upd 32: ragged front sizes, partial 128-row tiles, fronts of
+    one own tile) and with the panel steps alone (0), against SciPy's local direct solve."""
+    monkeypatch.setenv("HZ_FACTOR_TC_MIN", min_upd)
+    p = W.small_problem(28, 4, 2, seed=41, R=1)
+    s = make_solver(hz, p, "mixed")
+    parts = D.layer_partition(p.n, p.npml, p.n_layers)
+    rng = np.random.default_rng(9)
+    for ell in range(p.n_layers):
+        lo, hi, zlo, zhi = s.layer_info(ell)
+        H = D.local_operator(p.m, p.omega, ell, parts, p.npml, p.npml, p.C).tocsc()
+        g = rng.standard_normal((3, H.shape[0])) + 1j * rng.standard_normal((3, H.shape[0]))
+        w_ref = spla.splu(H).solve(g.T).T
+        w = s.layer_solve(ell, cuda(g.reshape(3, zhi - zlo + 1, p.n, p.n))).cpu().numpy().reshape(3, -1)
+        assert rel(w, w_ref) < STAGE_TOL["mixed"], (ell, rel(w, w_ref))
+    s.close()
+
+
+def test_tensor_core_factorization_end_to_end(hz, monkeypatch):
+    """A mixed-precision solve whose factors come from the tensor-core products on every eligible
+    front matches the global direct solve to the end-to-end tolerance."""
+    monkeypatch.setenv("HZ_FACTOR_TC_MIN", "32")
+    p = W.small_problem(24, 4, 3, seed=42, R=3)
+    f = p.rhs()
+    u_ref = direct.solve(p.m, p.omega, p.npml, p.C, f)
+    s = make_solver(hz, p, "mixed")
+    u, info, _ = s.solve(cuda(f))
+    for r in range(p.R):
+        assert rel(u[r].cpu().numpy(), u_ref[r]) < E2E_TOL["mixed"]
+    s.close()
