@@ -111,6 +111,9 @@ void hz_default_opts(hz_precision prec, hz_solve_opts* opts);
  *                     walking the work items) instead of one block per work item (0)
  *   HZ_AUTOTUNE=0     keep the fixed defaults; HZ_GRAPHS=0 no CUDA-graph replay;
  *   HZ_LEAF           nested-dissection leaf size (cells, default 256)
+ *   HZ_SPARSE         substitutions inside M_pol, the preconditioner and the polarized right-hand
+ *                     side skip the products of subtrees that hold none of a layer's interface
+ *                     planes (3, default: forward and backward; 2: backward only; 0: never)
  *   HZ_FACTOR_PROFILE=1  time every factorization launch by kernel kind (hz_factor_report)
  *   HZ_FACTOR_TC_MIN  complex64 fronts with at least this many update unknowns (default 128)
  *                     compute L21 and their Schur complement on the tensor cores; 0: never
@@ -279,7 +282,8 @@ hz_status hz_volume_residual_noalloc(hz_handle* h, const double* rhs, const doub
  * counterpart in the paper; it is the denominator of the tensor-core kernels' roofline).
  * One block per SM issues tcgen05 MMAs (M = 128, N = n, one instruction's K) from operands
  * resident in shared memory, with no global-memory traffic, for about `seconds` seconds.
- *   kind     0: kind::tf32 (tf32 x tf32 -> f32, K = 8); 1: kind::f16 with bf16 operands (K = 16)
+ *   kind     0: kind::tf32 (tf32 x tf32 -> f32, K = 8); 1: kind::f16 with bf16 operands (K = 16);
+ *            2: kind::tf32 with the A operand read from tensor memory instead of shared memory
  *   n        64, 128 or 256
  *   seconds  0 < seconds <= 30
  *   tflops   receives 2*128*n*K flops per MMA x MMAs / time, in TFLOP/s

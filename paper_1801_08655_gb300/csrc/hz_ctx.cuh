@@ -39,6 +39,7 @@ struct Batch {
     int min_t = 8;                              // output tiles a node product needs for the tensor cores
     int split = 3;                              // TF32 terms per real product on the tensor cores (3 or 1)
     int tc_cfg = 0;                             // tensor-core kernel: 0 one block per work item, 1 persistent
+    int sparse = 0;                             // products skipped away from the interface planes (get_batch)
     std::vector<long long> pair_off[4], pair_cnt[4];  // tensor-core tasks: two output tiles each
     Task* d_tasks = nullptr;
     void* d_jobs = nullptr;                     // JobDev<C>[njobs]
@@ -182,6 +183,8 @@ struct Ctx {
     int tc_min_tiles = 8;   // output tiles a node product needs to run on the tensor cores
     int tc_cfg = 0;         // untuned tensor-core kernel: 0 one block per work item, 1 persistent (HZ_TC_CFG)
     int precond_split = 3;  // TF32 terms of the tensor-core products inside the preconditioner (3 or 1)
+    int sparse_subst = 3;   // skip substitution products away from the interface planes where the
+                            // operator allows it (bit 0 forward, bit 1 backward; HZ_SPARSE)
     bool factor_prof = false;     // time every factorization launch by kernel kind (HZ_FACTOR_PROFILE=1)
     std::string factor_text;      // per-kind table of the last profiled factorization
     int factor_tc_min_upd = 128;  // complex64 fronts with at least this many update unknowns (and a

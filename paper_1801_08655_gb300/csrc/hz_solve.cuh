@@ -11,14 +11,19 @@ int tc_columns(int ldc);   // tensor-core column tile for this leading dimension
 void launch_level_tc(const Batch& b, int h, int mode, int ldc, int* flag, cudaStream_t st);
 int padded_ldc(bool is_double, int ncols);
 
-// Job set with per-level task lists, cached by layer list.
-template <class C> Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols, int split = 3);
+// Job set with per-level task lists, cached by layer list.  sparse: bit 0 skips the forward
+// products of nodes whose subtree holds none of the layer's interface planes (their right-hand
+// side, and so their forward result, is zero when the sources sit on those planes only); bit 1
+// skips the backward products of such nodes (no read-out below them when only those planes are
+// read).  0 solves everywhere.
+template <class C> Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols, int split = 3, int sparse = 0);
 // Build (or fetch) a batch with an explicit split-K depth and column chunk.
 template <class C> Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS, int CC, bool tc,
-                                       int KS_tc, int min_t, int split = 3, int tc_cfg = 0);
+                                       int KS_tc, int min_t, int split = 3, int tc_cfg = 0, int sparse = 0);
 // Autotune the substitution of this batch signature (times candidate split-K depths and column
 // chunks on zeroed slot vectors); a no-op once the signature is tuned or when tuning is off.
-template <class C> void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols, int split = 3);
+template <class C> void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols, int split = 3,
+                                     int sparse = 0);
 void free_batches(Ctx& ctx);
 
 // Forward/backward substitution for every job of the batch on ncols columns of the

@@ -29,6 +29,13 @@ __device__ inline uint64_t pk_desc(uint32_t saddr) {
     return d;
 }
 
+// A from tensor memory (address of the first of K columns holding the 128 x K operand, lane = row)
+__device__ inline void pk_mma_tmem_a(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}"
+                 :: "r"(d), "r"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
 template <int KIND>
 __device__ inline void pk_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     if (KIND == 0) {
@@ -42,7 +49,7 @@ __device__ inline void pk_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc
     }
 }
 
-// KIND 0: tf32 x tf32 -> f32; 1: bf16 x bf16 -> f32.
+// KIND 0: tf32 x tf32 -> f32; 1: bf16 x bf16 -> f32; 2: tf32 with the A operand in tensor memory.
 // Dynamic shared memory of the probe: operands and barrier use the first 12 KB; the rest only
 // keeps a second block off the SM, so that every SM runs exactly one issuing block.
 constexpr int PK_SMEM = 120 * 1024;
@@ -72,14 +79,29 @@ __global__ void __launch_bounds__(128, 1) k_tensor_peak(long long iters, int N, 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tptr;
+    // KIND 2: the A operand (128 lanes x 8 columns of 1/64) sits in tensor memory after the two
+    // accumulators (columns 256 + 8k .. for N <= 128; one accumulator of N = 256 ends at 256)
+    const uint32_t a_col = 384u;
+    if (KIND == 2) {
+        const uint32_t taddr = tmem + ((uint32_t)(32 * w) << 16) + a_col;
+        const uint32_t v1 = 0x3C800000u;
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                     :: "r"(taddr), "r"(v1), "r"(v1), "r"(v1), "r"(v1), "r"(v1), "r"(v1), "r"(v1), "r"(v1) : "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     bool ok = true;
     if (t == 0) {
-        const uint32_t fmt = KIND == 0 ? 2u : 1u;   // operand format: tf32 = 2 (kind::tf32), bf16 = 1 (kind::f16)
+        const uint32_t fmt = KIND == 1 ? 1u : 2u;   // operand format: tf32 = 2 (kind::tf32), bf16 = 1 (kind::f16)
         const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | (8u << 24);
         const uint64_t ad = pk_desc(pk_smem_u32(a_s)), bd = pk_desc(pk_smem_u32(b_s));
+        const uint32_t accw = N <= 128 ? 128u : 0u;   // second accumulator (N <= 128 only)
         for (long long i = 0; i < iters; ++i) {
-            const uint32_t acc = (uint32_t)(i & 1) * 256u;
-            pk_mma<KIND>(tmem + acc, ad, bd, idesc, i >= 2 ? 1u : 0u);
+            const uint32_t acc = (uint32_t)(i & 1) * accw;
+            if (KIND == 2) pk_mma_tmem_a(tmem + acc, tmem + a_col, bd, idesc, i >= 2 ? 1u : 0u);
+            else pk_mma<KIND>(tmem + acc, ad, bd, idesc, i >= 2 ? 1u : 0u);
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                      :: "r"(pk_smem_u32(&bar)));
@@ -110,7 +132,7 @@ __global__ void __launch_bounds__(128, 1) k_tensor_peak(long long iters, int N, 
 
 extern "C" hz_status hz_tensor_peak(int32_t kind, int32_t n, double seconds, double* tflops, double* ms) {
     using namespace hz;
-    if ((kind != 0 && kind != 1) || (n != 64 && n != 128 && n != 256) || !(seconds > 0.0) || seconds > 30.0 ||
+    if ((kind < 0 || kind > 2) || (n != 64 && n != 128 && n != 256) || !(seconds > 0.0) || seconds > 30.0 ||
         !tflops)
         return HZ_ERR_ARG;
     int dev = 0, sms = 0;
@@ -119,7 +141,7 @@ extern "C" hz_status hz_tensor_peak(int32_t kind, int32_t n, double seconds, dou
         cudaGetLastError();
         return HZ_ERR_CUDA;
     }
-    const int K = kind == 0 ? 8 : 16;
+    const int K = kind == 1 ? 16 : 8;
     const double flops_per_mma = 2.0 * 128.0 * n * K;
     int* flag = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -132,7 +154,8 @@ extern "C" hz_status hz_tensor_peak(int32_t kind, int32_t n, double seconds, dou
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     if (cudaFuncSetAttribute(k_tensor_peak<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, PK_SMEM) != cudaSuccess ||
-        cudaFuncSetAttribute(k_tensor_peak<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, PK_SMEM) != cudaSuccess) {
+        cudaFuncSetAttribute(k_tensor_peak<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, PK_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(k_tensor_peak<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, PK_SMEM) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(flag);
         return HZ_ERR_CUDA;
@@ -140,7 +163,8 @@ extern "C" hz_status hz_tensor_peak(int32_t kind, int32_t n, double seconds, dou
     auto run = [&](long long iters) -> float {
         cudaEventRecord(e0);
         if (kind == 0) k_tensor_peak<0><<<sms, 128, PK_SMEM>>>(iters, n, flag);
-        else k_tensor_peak<1><<<sms, 128, PK_SMEM>>>(iters, n, flag);
+        else if (kind == 1) k_tensor_peak<1><<<sms, 128, PK_SMEM>>>(iters, n, flag);
+        else k_tensor_peak<2><<<sms, 128, PK_SMEM>>>(iters, n, flag);
         g_launch_count.fetch_add(1, std::memory_order_relaxed);
         cudaEventRecord(e1);
         cudaEventSynchronize(e1);

@@ -454,24 +454,25 @@ static bool tc_node(int mode, const Node& nd, int min_tiles) {
     return out_t >= min_tiles && red_t >= (min_tiles <= 2 ? 1 : 2);
 }
 
-static std::string tune_key(const Ctx& ctx, const std::vector<int>& layers, int ldc, int split) {
+static std::string tune_key(const Ctx& ctx, const std::vector<int>& layers, int ldc, int split, int sparse) {
     std::vector<int> shapes;
     for (int l : layers) shapes.push_back(ctx.layers[l].shape);
     std::sort(shapes.begin(), shapes.end());
-    std::string key = "n" + std::to_string(ldc) + (split == 1 ? "s1" : "") + ":";
+    std::string key = "n" + std::to_string(ldc) + (split == 1 ? "s1" : "") + (sparse ? "p" + std::to_string(sparse) : "") + ":";
     for (int s : shapes) key += std::to_string(s) + ",";
     return key;
 }
 
 template <class C>
-Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols, int split) {
+Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols, int split, int sparse) {
     const bool dbl = sizeof(C) == 16;
     const int ldc = padded_ldc(dbl, ncols);
     const bool tc_ok = !dbl && tc_columns(ldc) > 0;
-    auto it = ctx.tuned.find(tune_key(ctx, layers, ldc, split));
+    auto it = ctx.tuned.find(tune_key(ctx, layers, ldc, split, sparse));
     if (it != ctx.tuned.end()) {
         const auto& ch = it->second;
-        return get_batch_cfg<C>(ctx, layers, ncols, ch.KS, ch.CC, tc_ok && ch.tc, ch.KS_tc, ch.min_t, split, ch.tc_cfg);
+        return get_batch_cfg<C>(ctx, layers, ncols, ch.KS, ch.CC, tc_ok && ch.tc, ch.KS_tc, ch.min_t, split, ch.tc_cfg,
+                                sparse);
     }
     // default: split the reductions when the batch alone cannot fill the GPU
     const int nchunks = ldc / chunk_cols(dbl, ncols);
@@ -479,15 +480,15 @@ Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols, int split)
     const bool tc = tc_ok && ctx.tc_mode == 1;
     const int nchunks_tc = tc ? ldc / tc_columns(ldc) : 1;
     const int KS_tc = ((long long)layers.size() * nchunks_tc >= 32) ? (1 << 30) : ctx.tc_ks;
-    return get_batch_cfg<C>(ctx, layers, ncols, KS, 0, tc, KS_tc, ctx.tc_min_tiles, split, ctx.tc_cfg);
+    return get_batch_cfg<C>(ctx, layers, ncols, KS, 0, tc, KS_tc, ctx.tc_min_tiles, split, ctx.tc_cfg, sparse);
 }
 
 template <class C>
-void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols, int split) {
+void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols, int split, int sparse) {
     const bool dbl = sizeof(C) == 16;
     const int ldc = padded_ldc(dbl, ncols);
     const bool tc_ok = !dbl && tc_columns(ldc) > 0;
-    const std::string key = tune_key(ctx, layers, ldc, split);
+    const std::string key = tune_key(ctx, layers, ldc, split, sparse);
     if (!ctx.autotune || ctx.tuned.count(key)) return;
     const int cc0 = chunk_cols(dbl, ncols);
     std::vector<Ctx::TuneChoice> cands;
@@ -513,7 +514,8 @@ void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols, int split
     ctx.prof = false;
     std::string log = key + " ->";
     for (const auto& cd : cands) {
-        Batch& b = get_batch_cfg<C>(ctx, layers, ncols, cd.KS, cd.CC, cd.tc != 0, cd.KS_tc, cd.min_t, split, cd.tc_cfg);
+        Batch& b = get_batch_cfg<C>(ctx, layers, ncols, cd.KS, cd.CC, cd.tc != 0, cd.KS_tc, cd.min_t, split, cd.tc_cfg,
+                                    sparse);
         for (size_t j = 0; j < b.vec_ptrs.size(); ++j)
             HZ_CUDA(cudaMemsetAsync(b.vec_ptrs[j].first, 0, (size_t)b.vec_rows[j] * ldc * sizeof(C), ctx.stream));
         substitute<C>(ctx, b, ncols, ctx.stream);  // warm-up
@@ -539,13 +541,13 @@ void ensure_tuned(Ctx& ctx, const std::vector<int>& layers, int ncols, int split
 
 template <class C>
 Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS, int CC, bool tc, int KS_tc,
-                     int min_t, int split, int tc_cfg) {
+                     int min_t, int split, int tc_cfg, int sparse) {
     const bool dbl = sizeof(C) == 16;
     const int ldc = padded_ldc(dbl, ncols);
     std::string key = "KS" + std::to_string(KS) + "C" + std::to_string(CC) + "n" + std::to_string(ldc) +
                       (tc ? "tc" + std::to_string(KS_tc) + "m" + std::to_string(min_t) + "s" + std::to_string(split) +
                                 "c" + std::to_string(tc_cfg)
-                          : "") + ":";
+                          : "") + "p" + std::to_string(sparse) + ":";
     for (int l : layers) key += std::to_string(l) + ",";
     auto it = ctx.batches.find(key);
     if (it != ctx.batches.end()) return it->second;
@@ -558,6 +560,7 @@ Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS
     b.min_t = min_t;
     b.split = split;
     b.tc_cfg = tc_cfg;
+    b.sparse = sparse;
     int H = 0;
     for (int l : layers) H = std::max(H, (int)ctx.shapes[ctx.layers[l].shape].levels.size());
     b.H = H;
@@ -574,11 +577,23 @@ Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS
         for (int k = k0; k < k1; k += ks) out.push_back(Task{j, nid, tile, k});
     };
     for (int j = 0; j < (int)layers.size(); ++j) {
-        const Shape& sh = ctx.shapes[ctx.layers[layers[j]].shape];
+        const Layer& ly = ctx.layers[layers[j]];
+        const Shape& sh = ctx.shapes[ly.shape];
+        // local z planes that carry the interface sources and read-outs of this layer (the plane
+        // pairs next to its internal interfaces); a node whose subtree box misses all of them has
+        // a zero forward result (sparse & 1) / no read-out below it (sparse & 2)
+        std::vector<int> planes;
+        if (layers[j] > 0) { planes.push_back(ly.lo - 1 - ly.zlo); planes.push_back(ly.lo - ly.zlo); }
+        if (layers[j] < ctx.L - 1) { planes.push_back(ly.hi - ly.zlo); planes.push_back(ly.hi + 1 - ly.zlo); }
         for (int h = 0; h < (int)sh.levels.size(); ++h)
             for (int nid : sh.levels[h]) {
                 const Node& nd = sh.nodes[nid];
+                bool touches = false;
+                for (int z : planes) touches = touches || (z >= nd.box[4] && z < nd.box[5]);
+                const bool fwd_on = !(sparse & 1) || touches;
+                const bool bwd_on = !(sparse & 2) || touches;
                 for (int mode = 0; mode < 4; ++mode) {
+                    if ((mode == FA || mode == FB) ? !fwd_on : !bwd_on) continue;
                     const int out_t = mode == 1 ? nd.upd_t : nd.own_t;
                     const bool on_tc = tc && tc_node(mode, nd, b.min_t);
                     // stored factor entries this product reads (triangular L^{-1} or L21)
@@ -652,11 +667,15 @@ Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS
         jobs.push_back(jd);
         b.vec_ptrs.push_back({ctx.slot_acc[l], ctx.slot_x[l]});
         b.vec_rows.push_back(sh.N);
-        double entries = 0;
-        for (auto& nd : sh.nodes) entries += (double)nd.nown * (nd.nown + 1) / 2.0 + (double)nd.nown * nd.nupd;
-        b.alg_bytes += 2.0 * entries * sizeof(C);
-        b.flops_per_col += sh.solve_flops_per_col;
     }
+    // algorithmic work of the products this batch runs (each stored factor entry of an active
+    // product read once, 8 real flops per entry and column)
+    for (int k = 0; k < 2; ++k)
+        for (int mode = 0; mode < 4; ++mode)
+            for (int h = 0; h < H; ++h) {
+                b.alg_bytes += b.lvl_bytes[k][mode][h];
+                b.flops_per_col += b.lvl_flops[k][mode][h];
+            }
     HZ_CUDA(cudaMalloc(&b.d_jobs, jobs.size() * sizeof(JobDev<C>)));
     HZ_CUDA(cudaMemcpyAsync(b.d_jobs, jobs.data(), jobs.size() * sizeof(JobDev<C>), cudaMemcpyHostToDevice,
                             ctx.stream));
@@ -674,11 +693,11 @@ void free_batches(Ctx& ctx) {
 
 template void substitute<float2>(Ctx&, const Batch&, int, cudaStream_t);
 template void substitute<double2>(Ctx&, const Batch&, int, cudaStream_t);
-template Batch& get_batch<float2>(Ctx&, const std::vector<int>&, int, int);
-template Batch& get_batch<double2>(Ctx&, const std::vector<int>&, int, int);
-template Batch& get_batch_cfg<float2>(Ctx&, const std::vector<int>&, int, int, int, bool, int, int, int, int);
-template Batch& get_batch_cfg<double2>(Ctx&, const std::vector<int>&, int, int, int, bool, int, int, int, int);
-template void ensure_tuned<float2>(Ctx&, const std::vector<int>&, int, int);
-template void ensure_tuned<double2>(Ctx&, const std::vector<int>&, int, int);
+template Batch& get_batch<float2>(Ctx&, const std::vector<int>&, int, int, int);
+template Batch& get_batch<double2>(Ctx&, const std::vector<int>&, int, int, int);
+template Batch& get_batch_cfg<float2>(Ctx&, const std::vector<int>&, int, int, int, bool, int, int, int, int, int);
+template Batch& get_batch_cfg<double2>(Ctx&, const std::vector<int>&, int, int, int, bool, int, int, int, int, int);
+template void ensure_tuned<float2>(Ctx&, const std::vector<int>&, int, int, int);
+template void ensure_tuned<double2>(Ctx&, const std::vector<int>&, int, int, int);
 
 }  // namespace hz

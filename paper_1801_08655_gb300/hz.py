@@ -348,7 +348,7 @@ def solve_group(solvers, rhs_list, opts: Optional[SolveOpts] = None, allow_nocon
 def tensor_peak(kind: str = "tf32", n: int = 128, seconds: float = 1.0):
     """Measured dense tcgen05 MMA rate of the current device (hz_tensor_peak): (TFLOP/s, ms)."""
     tf, ms = ct.c_double(), ct.c_double()
-    st = load().hz_tensor_peak({"tf32": 0, "bf16": 1}[kind], n, seconds, ct.byref(tf), ct.byref(ms))
+    st = load().hz_tensor_peak({"tf32": 0, "bf16": 1, "tf32_tmem_a": 2}[kind], n, seconds, ct.byref(tf), ct.byref(ms))
     if st != HZ_OK:
         raise HzError(st, f"hz_tensor_peak({kind}, {n}) failed")
     return tf.value, ms.value

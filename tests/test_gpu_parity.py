@@ -455,3 +455,26 @@ def test_tensor_core_factorization_end_to_end(hz, monkeypatch):
     for r in range(p.R):
         assert rel(u[r].cpu().numpy(), u_ref[r]) < E2E_TOL["mixed"]
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sparse_substitution_matches_full(hz, precision, monkeypatch):
+    """Skipping the products of subtrees away from the interface planes (HZ_SPARSE=3, forward
+    and backward) changes neither M_pol, nor the preconditioner, nor the polarized right-hand
+    side, nor the end-to-end solution beyond rounding (the skipped products are exactly zero or
+    unread); checked on 6 layers of a smooth medium with thick local pads."""
+    p = W.small_problem(22, 4, 6, seed=43, R=3)
+    rng = np.random.default_rng(11)
+    out = {}
+    for flag in ("0", "3"):
+        monkeypatch.setenv("HZ_SPARSE", flag)
+        s = make_solver(hz, p, precision)
+        f = cuda(p.rhs())
+        x = torch.from_numpy(rng.standard_normal(s.trace_shape(p.R)) + 1j * rng.standard_normal(s.trace_shape(p.R))).cuda()
+        out[flag] = dict(fpol=s.polarized_rhs(f).cpu().numpy(), mpol=s.apply_mpol(x).cpu().numpy(),
+                         prec=s.apply_precond(x).cpu().numpy(), u=s.solve(f)[0].cpu().numpy())
+        rng = np.random.default_rng(11)
+        s.close()
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    for k in ("fpol", "mpol", "prec", "u"):
+        assert rel(out["3"][k], out["0"][k]) < tol, (k, rel(out["3"][k], out["0"][k]))

@@ -1,6 +1,6 @@
 """GPU test of the tensor-pipe peak probe (hz_tensor_peak): the measured dense MMA rates are in
-the range the hardware allows (TF32 at half the bf16 rate; neither above the SM clock limit), and
-bad arguments come back as statuses."""
+the range the hardware allows (TF32 at half the bf16 rate; neither above the SM clock limit; the
+same TF32 rate with the A operand in tensor memory), and bad arguments come back as statuses."""
 import ctypes as ct
 
 import pytest
@@ -21,7 +21,10 @@ def test_tensor_peak_probe():
     assert 300.0 < tf32 < 1.05 * 152 * 2.07e9 * 4096 / 1e12
     assert 600.0 < bf16 < 1.05 * 152 * 2.07e9 * 8192 / 1e12
     assert 0.4 < tf32 / bf16 < 0.6
+    # the A operand read from tensor memory instead of shared memory: the same rate
+    tmem_a, _ = hz.tensor_peak("tf32_tmem_a", 128, 0.3)
+    assert 0.9 < tmem_a / tf32 < 1.1
     lib = hz.load()
     out = ct.c_double()
-    assert lib.hz_tensor_peak(2, 128, 0.1, ct.byref(out), None) == hz.HZ_ERR_ARG
+    assert lib.hz_tensor_peak(3, 128, 0.1, ct.byref(out), None) == hz.HZ_ERR_ARG
     assert lib.hz_tensor_peak(0, 96, 0.1, ct.byref(out), None) == hz.HZ_ERR_ARG
