@@ -81,3 +81,21 @@ def test_symbolic_rejects_a_tree_that_does_not_separate():
     Ap.sort_indices()
     with pytest.raises(ValueError):
         mf.symbolic(nodes, Ap)
+
+
+def test_stored_128cube_reference_is_consistent():
+    """The stored 128^3 oracle values (tests/golden/make_golden_cfg3.py) belong to the 128^3
+    workload's sources, come from a solve whose residual is at rounding level, and are
+    self-consistent (samples bounded by the full norms, physical-region norms below the full ones,
+    sketches of the right magnitude: E|<w, u>|^2 = ||u||^2)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cfg3_128cube_layered_block.npz")
+    ref = np.load(path)
+    p = W.config(3)
+    assert np.array_equal(ref["sources"], p.sources)
+    assert ref["u"].shape == (p.R, ref["idx"].size) and ref["sketch"].shape == (p.R, int(ref["sketch_k"]))
+    assert np.all(ref["relres"] < 1e-12)
+    assert np.all(np.linalg.norm(ref["u"], axis=1) < ref["norms"])
+    assert np.all(ref["norms_phys"] < ref["norms"])
+    ratio = np.sqrt(np.mean(np.abs(ref["sketch"]) ** 2, axis=1)) / ref["norms"]
+    assert np.all((ratio > 0.4) & (ratio < 2.0)), ratio.min()
