@@ -115,6 +115,9 @@ void hz_default_opts(hz_precision prec, hz_solve_opts* opts);
  *                     side skip the products of subtrees that hold none of a layer's interface
  *                     planes (3, default: forward and backward; 2: backward only; 0: never)
  *   HZ_FACTOR_PROFILE=1  time every factorization launch by kernel kind (hz_factor_report)
+ *   HZ_TC_WAIT_POLLS  poll limit of the tensor-core kernels' pipeline waits (default 2^26, and
+ *                     2 s of wall time); a tiny value makes them give up at once, which a solve
+ *                     reports as HZ_ERR_TIMEOUT (the blocks still drain their own copies and MMAs)
  *   HZ_FACTOR_TC_MIN  complex64 fronts with at least this many update unknowns (default 128)
  *                     compute L21 and their Schur complement on the tensor cores; 0: never
  */

@@ -538,11 +538,12 @@ void factor_layers(Ctx& ctx) {
                     HZ_CUDA(cudaMemcpyAsync(d_items + it_l21.size(), it_schur.data(), it_schur.size() * sizeof(GemmItem),
                                             cudaMemcpyHostToDevice, st));
                     FP_BEGIN();
-                    launch_front_gemm(0, d_items, (long long)it_l21.size(), (const FrontGemmDesc*)d_gd, ctx.d_flag + 1, st);
+                    launch_front_gemm(0, d_items, (long long)it_l21.size(), (const FrontGemmDesc*)d_gd, ctx.d_flag + 1,
+                                      ctx.tc_wait_polls, st);
                     FP_END(FK_GEMM_L21);
                     FP_BEGIN();
                     launch_front_gemm(1, d_items + it_l21.size(), (long long)it_schur.size(), (const FrontGemmDesc*)d_gd,
-                                      ctx.d_flag + 1, st);
+                                      ctx.d_flag + 1, ctx.tc_wait_polls, st);
                     FP_END(FK_GEMM_SCHUR);
                 }
                 // 6. pack L21 (fronts factored by the panel steps alone)

@@ -94,7 +94,7 @@ __device__ __forceinline__ void convert_operand(const unsigned char* rb, const f
 
 template <int MODE>
 __global__ void __launch_bounds__(G_THREADS, 1)
-k_front_gemm(const GemmItem* __restrict__ items, const FrontGemmDesc* __restrict__ fronts, int* flag) {
+k_front_gemm(const GemmItem* __restrict__ items, const FrontGemmDesc* __restrict__ fronts, int* flag, long long polls) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* conv = smem;                  // [2][G_CONV]
     unsigned char* raw = smem + 2 * G_CONV;      // [2][G_RAW]
@@ -105,6 +105,7 @@ k_front_gemm(const GemmItem* __restrict__ items, const FrontGemmDesc* __restrict
     uint64_t* conv_empty = bars + 6;  // [2] MMAs of the buffer done (tcgen05.commit)
     uint32_t* tptr = (uint32_t*)(bars + 8);
     volatile int* abort = (volatile int*)(bars + 8) + 1;
+    volatile int* committed = (volatile int*)(bars + 8) + 2;   // stages whose MMAs were committed
 
     const GemmItem it = items[blockIdx.x];
     const FrontGemmDesc f = fronts[it.front];
@@ -124,6 +125,7 @@ k_front_gemm(const GemmItem* __restrict__ items, const FrontGemmDesc* __restrict
             mbar_init(conv_empty + b, 1);
         }
         *abort = 0;
+        *committed = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -136,7 +138,7 @@ k_front_gemm(const GemmItem* __restrict__ items, const FrontGemmDesc* __restrict
         // ------------------------------------------------------------ loaders
         for (int s = 0; s < nst && ok; ++s) {
             const int slot = s & 1, use = s >> 1;
-            if (s >= 2) ok = mbar_wait(smem_u32(raw_empty + slot), (uint32_t)((use - 1) & 1), abort);
+            if (s >= 2) ok = mbar_wait(smem_u32(raw_empty + slot), (uint32_t)((use - 1) & 1), abort, polls);
             if (!ok) break;
             unsigned char* rb = raw + slot * G_RAW;
             const int kt = s >> 1, hk = s & 1;
@@ -178,8 +180,8 @@ k_front_gemm(const GemmItem* __restrict__ items, const FrontGemmDesc* __restrict
         const int ct = t - NLOAD;
         for (int s = 0; s < nst && ok; ++s) {
             const int slot = s & 1, use = s >> 1;
-            ok = mbar_wait(smem_u32(raw_full + slot), (uint32_t)(use & 1), abort);
-            if (ok && s >= 2) ok = mbar_wait(smem_u32(conv_empty + slot), (uint32_t)((use - 1) & 1), abort);
+            ok = mbar_wait(smem_u32(raw_full + slot), (uint32_t)(use & 1), abort, polls);
+            if (ok && s >= 2) ok = mbar_wait(smem_u32(conv_empty + slot), (uint32_t)((use - 1) & 1), abort, polls);
             if (!ok) break;
             const unsigned char* rb = raw + slot * G_RAW;
             unsigned char* cv = conv + slot * G_CONV;
@@ -194,18 +196,20 @@ k_front_gemm(const GemmItem* __restrict__ items, const FrontGemmDesc* __restrict
         // ------------------------------------------------------------ MMA issuer
         for (int s = 0; s < nst && ok; ++s) {
             const int cb = s & 1, use = s >> 1;
-            ok = mbar_wait(smem_u32(conv_full + cb), (uint32_t)(use & 1), abort);
+            ok = mbar_wait(smem_u32(conv_full + cb), (uint32_t)(use & 1), abort, polls);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             mma_stage<GN, 3>(smem_u32(conv + cb * G_CONV), tm_r, tm_i, s == 0);
             mma_commit(conv_empty + cb);
+            *committed = s + 1;
         }
     }
 
     ok = __syncthreads_and(ok) != 0;
     bool done = true;
-    if (nst > 0) {   // the last stage's MMAs, waited for even after an abort
-        const int sl = nst - 1;
+    const int ncommit = *committed;
+    if (ncommit > 0) {   // the last committed stage's MMAs, waited for even after an abort
+        const int sl = ncommit - 1;
         int no_abort = 0;
         const bool got = mbar_wait(smem_u32(conv_empty + (sl & 1)), (uint32_t)((sl >> 1) & 1), &no_abort);
         done = __syncthreads_and(got) != 0;
@@ -285,7 +289,7 @@ void front_gemm_items(const std::vector<FrontGemmDesc>& fr, std::vector<GemmItem
 }
 
 void launch_front_gemm(int mode, const GemmItem* d_items, long long n, const FrontGemmDesc* d_fronts, int* flag,
-                       cudaStream_t st) {
+                       long long polls, cudaStream_t st) {
     if (n <= 0) return;
     static bool attr[2] = {false, false};
     if (!attr[mode]) {
@@ -298,9 +302,9 @@ void launch_front_gemm(int mode, const GemmItem* d_items, long long n, const Fro
     for (long long b0 = 0; b0 < n; b0 += 65535LL * 16) {
         const unsigned grid = (unsigned)std::min<long long>(n - b0, 65535LL * 16);
         if (mode == GEMM_L21)
-            k_front_gemm<GEMM_L21><<<grid, G_THREADS, G_SMEM, st>>>(d_items + b0, d_fronts, flag);
+            k_front_gemm<GEMM_L21><<<grid, G_THREADS, G_SMEM, st>>>(d_items + b0, d_fronts, flag, polls);
         else
-            k_front_gemm<GEMM_SCHUR><<<grid, G_THREADS, G_SMEM, st>>>(d_items + b0, d_fronts, flag);
+            k_front_gemm<GEMM_SCHUR><<<grid, G_THREADS, G_SMEM, st>>>(d_items + b0, d_fronts, flag, polls);
         HZ_CHECK_LAUNCH();
     }
 }

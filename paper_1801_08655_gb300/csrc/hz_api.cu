@@ -425,6 +425,7 @@ hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz
         if (const char* e = std::getenv("HZ_FACTOR_TC_MIN")) c.factor_tc_min_upd = std::max(0, std::atoi(e));
         if (const char* e = std::getenv("HZ_FACTOR_PROFILE")) c.factor_prof = std::atoi(e) != 0;
         if (const char* e = std::getenv("HZ_SPARSE")) c.sparse_subst = std::max(0, std::min(3, std::atoi(e)));
+        if (const char* e = std::getenv("HZ_TC_WAIT_POLLS")) c.tc_wait_polls = std::max(1LL, std::atoll(e));
         HZ_CUDA(cudaDeviceSynchronize());  // uploads complete before any work on the stream
         *out = h;
         return HZ_OK;
@@ -564,6 +565,7 @@ hz_status hz_create_shared(hz_handle* src, void* stream, hz_handle** out) {
         c.d_sz_n = s.d_sz_n; c.d_isz_h = s.d_isz_h; c.d_m = s.d_m;
         c.tc_mode = s.tc_mode; c.tc_ks = s.tc_ks; c.tc_min_tiles = s.tc_min_tiles; c.precond_split = s.precond_split; c.tc_cfg = s.tc_cfg;
         c.sparse_subst = s.sparse_subst;
+        c.tc_wait_polls = s.tc_wait_polls;
         c.autotune = s.autotune; c.use_graphs = s.use_graphs;
         c.tuned = s.tuned;
         c.factored = true;

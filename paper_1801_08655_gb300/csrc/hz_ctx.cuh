@@ -40,6 +40,7 @@ struct Batch {
     int split = 3;                              // TF32 terms per real product on the tensor cores (3 or 1)
     int tc_cfg = 0;                             // tensor-core kernel: 0 one block per work item, 1 persistent
     int sparse = 0;                             // products skipped away from the interface planes (get_batch)
+    long long wait_polls = 1LL << 26;           // poll limit of the tensor-core kernels' pipeline waits
     std::vector<long long> pair_off[4], pair_cnt[4];  // tensor-core tasks: two output tiles each
     Task* d_tasks = nullptr;
     void* d_jobs = nullptr;                     // JobDev<C>[njobs]
@@ -183,6 +184,8 @@ struct Ctx {
     int tc_min_tiles = 8;   // output tiles a node product needs to run on the tensor cores
     int tc_cfg = 0;         // untuned tensor-core kernel: 0 one block per work item, 1 persistent (HZ_TC_CFG)
     int precond_split = 3;  // TF32 terms of the tensor-core products inside the preconditioner (3 or 1)
+    long long tc_wait_polls = 1LL << 26;  // poll limit of the tensor-core pipeline waits (HZ_TC_WAIT_POLLS:
+                                          // a small value makes the waits give up, to test that path)
     int sparse_subst = 3;   // skip substitution products away from the interface planes where the
                             // operator allows it (bit 0 forward, bit 1 backward; HZ_SPARSE)
     bool factor_prof = false;     // time every factorization launch by kernel kind (HZ_FACTOR_PROFILE=1)
@@ -214,7 +217,7 @@ bool front_gemm_eligible(int nown, int nupd, int min_upd);
 void front_gemm_items(const std::vector<FrontGemmDesc>& fronts, std::vector<GemmItem>& l21,
                       std::vector<GemmItem>& schur);
 void launch_front_gemm(int mode, const GemmItem* d_items, long long n, const FrontGemmDesc* d_fronts, int* flag,
-                       cudaStream_t st);
+                       long long polls, cudaStream_t st);
 
 }  // namespace hz
 

@@ -561,6 +561,7 @@ Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS
     b.split = split;
     b.tc_cfg = tc_cfg;
     b.sparse = sparse;
+    b.wait_polls = ctx.tc_wait_polls;
     int H = 0;
     for (int l : layers) H = std::max(H, (int)ctx.shapes[ctx.layers[l].shape].levels.size());
     b.H = H;

@@ -254,7 +254,7 @@ template <int NT> struct OneLayout {
 template <int NT, int MODE, int SPLIT>
 __global__ void __launch_bounds__(OneLayout<NT>::NTHREADS, 1)
 k_subst_tc(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ jobs, int ldc, int nchunks, int KS,
-           int* flag) {
+           int* flag, long long polls) {
     using RG = Ring<NT>;
     using LY = OneLayout<NT>;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -269,6 +269,7 @@ k_subst_tc(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ jo
     uint64_t* conv_empty = bars + 6;  // [2] MMAs of the buffer done (tcgen05.commit)
     uint32_t* tptr = (uint32_t*)(bars + 8);
     volatile int* abort = (volatile int*)(bars + 8) + 1;
+    volatile int* committed = (volatile int*)(bars + 8) + 2;   // stages whose MMAs were committed
 
     const Item it = decode<NT, MODE>(tasks, jobs, blockIdx.x, nchunks, KS);
     const int t = threadIdx.x, w = t >> 5, l = t & 31;
@@ -287,6 +288,7 @@ k_subst_tc(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ jo
             mbar_init(conv_empty + b, 1);
         }
         *abort = 0;
+        *committed = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -300,7 +302,7 @@ k_subst_tc(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ jo
         for (int s = 0; s < nst && ok; ++s) {
             const int slot = s & 1, use = s >> 1;
             const Vrows<NT> next = stage_rows<NT, MODE>(it, s + 1, t);   // looked up ahead
-            if (s >= 2) ok = mbar_wait(smem_u32(raw_empty + slot), (uint32_t)((use - 1) & 1), abort);
+            if (s >= 2) ok = mbar_wait(smem_u32(raw_empty + slot), (uint32_t)((use - 1) & 1), abort, polls);
             if (!ok) break;
             load_stage<NT, MODE>(raw + slot * RG::RAW, it, s, ldc, t, rows);
             cp_async_arrive(raw_full + slot);
@@ -317,8 +319,8 @@ k_subst_tc(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ jo
         const int ct = t - NLOAD;
         for (int s = 0; s < nst && ok; ++s) {
             const int slot = s & 1, use = s >> 1;
-            ok = mbar_wait(smem_u32(raw_full + slot), (uint32_t)(use & 1), abort);
-            if (ok && s >= 2) ok = mbar_wait(smem_u32(conv_empty + slot), (uint32_t)((use - 1) & 1), abort);
+            ok = mbar_wait(smem_u32(raw_full + slot), (uint32_t)(use & 1), abort, polls);
+            if (ok && s >= 2) ok = mbar_wait(smem_u32(conv_empty + slot), (uint32_t)((use - 1) & 1), abort, polls);
             if (!ok) break;
             convert_stage<NT, MODE, SPLIT>(raw + slot * RG::RAW, conv + slot * RG::CONV, ct);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -328,19 +330,21 @@ k_subst_tc(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ jo
     } else if (l == 0) {
         for (int s = 0; s < nst && ok; ++s) {
             const int cb = s & 1, use = s >> 1;
-            ok = mbar_wait(smem_u32(conv_full + cb), (uint32_t)(use & 1), abort);
+            ok = mbar_wait(smem_u32(conv_full + cb), (uint32_t)(use & 1), abort, polls);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             mma_stage<NT, SPLIT>(smem_u32(conv + cb * RG::CONV), tm_r, tm_i, s == 0);
             mma_commit(conv_empty + cb);
+            *committed = s + 1;
         }
     }
 
     // every role arrives here (their waits are bounded); make the outcome block-uniform
     ok = __syncthreads_and(ok) != 0;
     bool done = true;
-    if (nst > 0) {   // the last stage's MMAs, waited for even after an abort
-        const int sl = nst - 1;
+    const int ncommit = *committed;
+    if (ncommit > 0) {   // the last committed stage's MMAs, waited for even after an abort
+        const int sl = ncommit - 1;
         int no_abort = 0;
         const bool got = mbar_wait(smem_u32(conv_empty + (sl & 1)), (uint32_t)((sl >> 1) & 1), &no_abort);
         done = __syncthreads_and(got) != 0;
@@ -429,7 +433,7 @@ template <int NT> struct PLayout {
 template <int NT, int MODE, int SPLIT>
 __global__ void __launch_bounds__(PLayout<NT>::NTHREADS, 1)
 k_subst_tcp(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ jobs, int ldc, int nchunks, int KS,
-            long long nitems, int* flag) {
+            long long nitems, int* flag, long long polls) {
     using RG = Ring<NT>;
     using LY = PLayout<NT>;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -494,7 +498,7 @@ k_subst_tcp(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ j
                 Vrows<NT> next_rows;
                 if (s + 1 < cur.nst) next_rows = stage_rows<NT, MODE>(cur, s + 1, t);
                 else if (nxt_item < nitems) next_rows = stage_rows<NT, MODE>(nxt, 0, t);
-                if (gs >= 2) ok = mbar_wait(smem_u32(raw_empty + slot), (uint32_t)((use - 1) & 1), abort);
+                if (gs >= 2) ok = mbar_wait(smem_u32(raw_empty + slot), (uint32_t)((use - 1) & 1), abort, polls);
                 if (!ok) break;
                 load_stage<NT, MODE>(raw + slot * RG::RAW, cur, s, ldc, t, rows);
                 cp_async_arrive(raw_full + slot);
@@ -514,8 +518,8 @@ k_subst_tcp(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ j
             for (int s = 0; s < nst && ok; ++s, ++gs) {
                 const int slot = (int)(gs & 1);
                 const long long use = gs >> 1;
-                ok = mbar_wait(smem_u32(raw_full + slot), (uint32_t)(use & 1), abort);
-                if (ok && gs >= 2) ok = mbar_wait(smem_u32(conv_empty + slot), (uint32_t)((use - 1) & 1), abort);
+                ok = mbar_wait(smem_u32(raw_full + slot), (uint32_t)(use & 1), abort, polls);
+                if (ok && gs >= 2) ok = mbar_wait(smem_u32(conv_empty + slot), (uint32_t)((use - 1) & 1), abort, polls);
                 if (!ok) break;
                 convert_stage<NT, MODE, SPLIT>(raw + slot * RG::RAW, conv + slot * RG::CONV, ct);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -533,13 +537,13 @@ k_subst_tcp(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ j
                 const int nst = nst_next;   // decoded one item ahead
                 if (item + gridDim.x < nitems) nst_next = decode<NT, MODE>(tasks, jobs, item + gridDim.x, nchunks, KS).nst;
                 const int b = nit & 1;
-                if (nit >= 2) ok = mbar_wait(smem_u32(acc_empty + b), (uint32_t)(((nit >> 1) - 1) & 1), abort);
+                if (nit >= 2) ok = mbar_wait(smem_u32(acc_empty + b), (uint32_t)(((nit >> 1) - 1) & 1), abort, polls);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t tm_r = tmem + (uint32_t)(b * 2 * NT), tm_i = tm_r + NT;
                 for (int s = 0; s < nst && ok; ++s, ++gs) {
                     const int cb = (int)(gs & 1);
-                    ok = mbar_wait(smem_u32(conv_full + cb), (uint32_t)((gs >> 1) & 1), abort);
+                    ok = mbar_wait(smem_u32(conv_full + cb), (uint32_t)((gs >> 1) & 1), abort, polls);
                     if (!ok) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     mma_stage<NT, SPLIT>(smem_u32(conv + cb * RG::CONV), tm_r, tm_i, s == 0);
@@ -571,7 +575,7 @@ k_subst_tcp(const Task* __restrict__ tasks, const JobDev<float2>* __restrict__ j
             const long long my_base = row_base<MODE>(it, 32 * q4 + l, ldc);
             float2 my_d = make_float2(0.f, 0.f);
             if (MODE == BA && my_base >= 0) my_d = it.jb.dinv[it.nd.own0 + it.o0 * TILE + 32 * q4 + l];
-            ok = mbar_wait(smem_u32(acc_full + b), (uint32_t)((nit >> 1) & 1), abort);
+            ok = mbar_wait(smem_u32(acc_full + b), (uint32_t)((nit >> 1) & 1), abort, polls);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -646,7 +650,7 @@ void launch_one(const Batch& b, const Task* tasks, long long n, const JobDev<flo
         }
         const long long grid = std::min<long long>(nitems, sm_count());
         k_subst_tcp<NT, MODE, SPLIT><<<(unsigned)grid, PLayout<NT>::NTHREADS, PLayout<NT>::TOTAL, st>>>(
-            tasks, jobs, ldc, nchunks, b.KS_tc, nitems, flag);
+            tasks, jobs, ldc, nchunks, b.KS_tc, nitems, flag, b.wait_polls);
     } else {
         static bool attr = false;
         if (!attr) {
@@ -655,7 +659,7 @@ void launch_one(const Batch& b, const Task* tasks, long long n, const JobDev<flo
             attr = true;
         }
         k_subst_tc<NT, MODE, SPLIT><<<(unsigned)nitems, OneLayout<NT>::NTHREADS, OneLayout<NT>::TOTAL, st>>>(
-            tasks, jobs, ldc, nchunks, b.KS_tc, flag);
+            tasks, jobs, ldc, nchunks, b.KS_tc, flag, b.wait_polls);
     }
     HZ_CHECK_LAUNCH();
 }

@@ -55,11 +55,13 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Bounded wait for the phase of the given parity: gives up (false) after WAIT_LIMIT polls,
+// Bounded wait for the phase of the given parity: gives up (false) after max_polls polls (the
+// pipeline waits take the launch's limit; waits that drain a block's own MMAs keep WAIT_LIMIT),
 // WAIT_NS of wall time, or as soon as another role of the block has raised *abort.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
+                                          long long max_polls = WAIT_LIMIT) {
     unsigned long long t0 = 0;
-    for (long long it = 0; it < WAIT_LIMIT; ++it) {
+    for (long long it = 0; it < max_polls; ++it) {
         uint32_t ok;
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
                      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");

@@ -478,3 +478,45 @@ def test_sparse_substitution_matches_full(hz, precision, monkeypatch):
     tol = 1e-12 if precision == "fp64" else 1e-5
     for k in ("fpol", "mpol", "prec", "u"):
         assert rel(out["3"][k], out["0"][k]) < tol, (k, rel(out["3"][k], out["0"][k]))
+
+
+def test_tensor_core_wait_timeout_is_a_status(hz, monkeypatch):
+    """A tensor-core pipeline wait that gives up ends the solve with HZ_ERR_TIMEOUT, not a fault or
+    a hang: with a poll limit of 1 (HZ_TC_WAIT_POLLS) the first waits of every block give up before
+    its MMAs are issued; each block still drains its own copies and committed MMAs and frees its
+    tensor memory.  The same holds for the factorization's tensor-core products (hz_factor).  A
+    fresh handle afterwards solves the same problem correctly."""
+    p = W.config(1)
+    rng = np.random.default_rng(1801 + 64)
+    lo, hi = p.npml, p.n - p.npml
+    src = np.stack([rng.integers(lo, hi, 64) for _ in range(3)], axis=1)
+    wide = W.Problem("timeout_24cube_R64", p.n, p.npml, p.n_layers, p.omega, p.C, p.m, src)
+    f = cuda(wide.rhs())
+    monkeypatch.setenv("HZ_SUBST_TC", "1")
+    monkeypatch.setenv("HZ_TC_MIN_TILES", "2")
+    monkeypatch.setenv("HZ_TC_WAIT_POLLS", "1")
+    # the factorization's tensor-core products give up too
+    monkeypatch.setenv("HZ_FACTOR_TC_MIN", "32")
+    s = hz.Solver(wide.m, wide.omega, wide.npml, wide.C, wide.n_layers, precision="mixed")
+    with pytest.raises(hz.HzError) as e:
+        s.factor()
+    assert e.value.status == hz.HZ_ERR_TIMEOUT, e.value
+    s.close()
+    # factored without them, the solve's tensor-core substitutions give up
+    monkeypatch.setenv("HZ_FACTOR_TC_MIN", "0")
+    s = make_solver(hz, wide, "mixed")
+    o = hz.default_opts("mixed")
+    o.max_iter, o.max_refine = 2, 0
+    with pytest.raises(hz.HzError) as e:
+        s.solve(f, o)
+    assert e.value.status == hz.HZ_ERR_TIMEOUT, e.value
+    s.close()
+    torch.cuda.synchronize()   # the context is still usable
+    monkeypatch.delenv("HZ_TC_WAIT_POLLS")
+    monkeypatch.delenv("HZ_FACTOR_TC_MIN")
+    u_ref = direct.solve(wide.m, wide.omega, wide.npml, wide.C, wide.rhs())
+    s = make_solver(hz, wide, "mixed")
+    u, info, _ = s.solve(f)
+    s.close()
+    for r in range(wide.R):
+        assert rel(u[r].cpu().numpy(), u_ref[r]) < E2E_TOL["mixed"]
