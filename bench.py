@@ -237,6 +237,7 @@ def run_ours(args):
     opts = hz.default_opts("mixed")
     opts.gmres_tol = args.gmres_tol
     opts.refine_tol = args.refine_tol
+    opts.krylov = 1 if args.krylov == "bicgstab" else 0
     infos = None
     for _ in range(args.warmup):
         _, infos, _ = s.solve(rhs, opts, u=u)
@@ -436,7 +437,8 @@ def run_ours(args):
                            "per": f"batch of {R} right-hand sides"},
             "gmres_iters": iters, "refinements": refin, "volume_relres_max": vol_res,
             "solve_opts": {"gmres_tol": opts.gmres_tol, "refine_tol": opts.refine_tol,
-                           "max_refine": opts.max_refine, "restart": opts.restart},
+                           "max_refine": opts.max_refine, "restart": opts.restart,
+                           "krylov": "bicgstab" if opts.krylov == 1 else "gmres"},
             "factor_s": factor_s, "factor_tflops": fstats["factor_flops"] / factor_s / 1e12,
             "oracle_error": oracle_err,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
@@ -472,6 +474,7 @@ def run_batched(args):
     opts = hz.default_opts("mixed")
     opts.gmres_tol = args.gmres_tol
     opts.refine_tol = args.refine_tol
+    opts.krylov = 1 if args.krylov == "bicgstab" else 0
     Rtot = sum(p.R for p in probs)
     for _ in range(args.warmup):
         hz.solve_group(solvers, rhs, opts)
@@ -520,6 +523,7 @@ def run_serving(args):
     opts = hz.default_opts("mixed")
     opts.gmres_tol = args.gmres_tol
     opts.refine_tol = args.refine_tol
+    opts.krylov = 1 if args.krylov == "bicgstab" else 0
     opts.restart = 6
     rec = W.point_sources_plane_grid(n, p, p + 2, 8, 8)
     recv = (rec[:, 0] * n + rec[:, 1]) * n + rec[:, 2]
@@ -582,6 +586,8 @@ def main():
                     help="print the per-phase, per-level substitution profile of the profiled solve (stderr)")
     ap.add_argument("--gmres-tol", type=float, default=1e-5)
     ap.add_argument("--refine-tol", type=float, default=1e-6)
+    ap.add_argument("--krylov", default="gmres", choices=["gmres", "bicgstab"],
+                    help="Krylov solver on the trace system (hz_solve_opts.krylov)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

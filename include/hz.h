@@ -74,6 +74,9 @@ typedef struct {
     int32_t max_iter;    /* total GMRES iterations cap (default 100) */
     double refine_tol;   /* mixed mode: stop refining when ||S f - A u|| <= refine_tol ||S f|| (default 1e-9) */
     int32_t max_refine;  /* mixed mode: maximum defect-correction passes (default 3) */
+    int32_t krylov;      /* Krylov solver on the trace system: 0 GMRES(restart) (default), 1 Bi-CGSTAB
+                            (two products P M_pol per iteration, six trace vectors per column instead
+                            of restart + 1; gmres_tol and max_iter apply to it as well) */
 } hz_solve_opts;
 
 typedef struct {

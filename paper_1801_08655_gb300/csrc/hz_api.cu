@@ -198,7 +198,7 @@ void do_solve(Ctx& c, const double2* rhs, int R, double2* u, const hz_solve_opts
     st_out = HZ_OK;
     try {
         if (c.prec == HZ_PREC_FP64) {
-            gmres_solve<double2>(c, rhs, true, R, u, o, inf.data());
+            krylov_solve<double2>(c, rhs, true, R, u, o, inf.data());
             op_volume_residual(c, rhs, true, u, R, nullptr, norms);
             d2h(c, hn.data(), norms, 2 * R * sizeof(double));
             for (int r = 0; r < R; ++r) {
@@ -207,7 +207,7 @@ void do_solve(Ctx& c, const double2* rhs, int R, double2* u, const hz_solve_opts
                 if (!std::isfinite(inf[r].volume_relres)) st_out = HZ_ERR_NONFINITE;
             }
         } else {
-            gmres_solve<float2>(c, rhs, true, R, u, o, inf.data());
+            krylov_solve<float2>(c, rhs, true, R, u, o, inf.data());
             double2* res = (double2*)dev_alloc((size_t)R * N3 * sizeof(double2));
             double2* du = (double2*)dev_alloc((size_t)R * N3 * sizeof(double2));
             try {
@@ -228,7 +228,7 @@ void do_solve(Ctx& c, const double2* rhs, int R, double2* u, const hz_solve_opts
                     std::vector<hz_solve_info> inf2(R);
                     hz_solve_opts o2 = o;
                     o2.gmres_tol = std::max(o.gmres_tol, std::min(1e-1, 0.1 * o.refine_tol / std::max(worst, 1e-300)));
-                    gmres_solve<float2>(c, res, false, R, du, o2, inf2.data());
+                    krylov_solve<float2>(c, res, false, R, du, o2, inf2.data());
                     k_axpy_vol<<<cdiv((long long)R * N3, 256), 256, 0, c.stream>>>(u, du, (long long)R * N3);
                     HZ_CHECK_LAUNCH();
                     ++passes;
@@ -299,6 +299,7 @@ void hz_default_opts(hz_precision prec, hz_solve_opts* o) {
     o->max_iter = 100;
     o->refine_tol = 1e-9;
     o->max_refine = 3;
+    o->krylov = 0;
 }
 
 hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz_pml* pml, int32_t n_layers,
@@ -483,7 +484,8 @@ hz_status hz_solve(hz_handle* h, const double* rhs, int32_t R, double* u, const 
     HZ_TRY(h, {
         hz_solve_opts o;
         if (opts) o = *opts; else hz_default_opts(h->ctx.prec, &o);
-        if (o.restart < 1 || o.max_iter < 1 || !(o.gmres_tol > 0)) throw Error{HZ_ERR_ARG, "solve options"};
+        if (o.restart < 1 || o.max_iter < 1 || !(o.gmres_tol > 0) || (o.krylov != 0 && o.krylov != 1))
+            throw Error{HZ_ERR_ARG, "solve options"};
         hz_status st = HZ_OK;
         do_solve(h->ctx, (const double2*)rhs, R, (double2*)u, o, info, st);
         if (st != HZ_OK) h->ctx.last_error = st == HZ_ERR_NONFINITE ? "non-finite result" : "did not converge";

@@ -44,5 +44,8 @@ void op_volume_residual(Ctx& ctx, const double2* f, bool scale, const double2* u
 struct GmresOut { int iters; double relres; };
 template <class C> void gmres_solve(Ctx& ctx, const double2* g, bool scale, int R, double2* u,
                                     const hz_solve_opts& o, hz_solve_info* info);
+// GMRES (o.krylov == 0) or Bi-CGSTAB (1) on the trace system
+template <class C> void krylov_solve(Ctx& ctx, const double2* g, bool scale, int R, double2* u,
+                                     const hz_solve_opts& o, hz_solve_info* info);
 
 }  // namespace hz

@@ -1025,7 +1025,213 @@ template void op_apply_precond<float2>(Ctx&, const double2*, int, double2*, doub
 template void op_apply_precond<double2>(Ctx&, const double2*, int, double2*, double2*);
 template void op_reconstruct<float2>(Ctx&, const double2*, bool, const double2*, int, double2*, bool);
 template void op_reconstruct<double2>(Ctx&, const double2*, bool, const double2*, int, double2*, bool);
+// ------------------------------------------------------------------------------------------
+// Bi-CGSTAB on the same left-preconditioned trace system P M_pol x = P f_pol (the paper's
+// remark on Krylov solvers in its Parallelization Strategies section: Bi-CGSTAB keeps a fixed,
+// small number of vectors where GMRES keeps its whole basis).  One process per column, FP64,
+// x0 = 0, shadow residual r^ = r0; per iteration two matrix-vector products:
+//   rho = <r^, r>;  beta = (rho / rho_old)(alpha / omega);  p = r + beta (p - omega v);
+//   v = A p;  alpha = rho / <r^, v>;  s = r - alpha v;  t = A s;  omega = <t, s> / <t, t>;
+//   x += alpha p + omega s;  r = s - omega t
+// with <a, b> = a^H b.  A column stops when ||r|| <= tol ||b|| or on a breakdown (a vanishing
+// <r^, r> or <r^, v>); stopped columns are no longer updated.
+// ------------------------------------------------------------------------------------------
+struct BicgScalars {
+    double2* dots;     // [R][4]: <r^, r>, <r^, v>, <t, s>, <t, t>
+    double2* rho_old;  // [R]
+    double2* alpha;    // [R]
+    double2* omega;    // [R]
+    double2* beta;     // [R]
+    double* nrm;       // [R] ||r||^2
+    double* resid;     // [R] ||r||
+    const double* b0;  // [R] ||b||^2
+    int* active;       // [R]
+};
+
+__device__ inline double2 cdivc(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+__global__ void k_bicg_init(BicgScalars s, int R, double tiny) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    s.rho_old[r] = make_double2(1.0, 0.0);
+    s.alpha[r] = make_double2(1.0, 0.0);
+    s.omega[r] = make_double2(1.0, 0.0);
+    s.resid[r] = sqrt(s.b0[r]);
+    s.active[r] = s.b0[r] > tiny * tiny;
+}
+
+// stage 0: beta from rho = <r^, r>; stage 1: alpha = rho / <r^, v>; stage 2: omega = <t,s>/<t,t>
+__global__ void k_bicg_scalars(BicgScalars s, int R, int stage, double tiny) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R || !s.active[r]) return;
+    const double2* d = s.dots + 4LL * r;
+    if (stage == 0) {
+        const double2 rho = d[0];
+        if (!(sqrt(rho.x * rho.x + rho.y * rho.y) > tiny)) { s.active[r] = 0; return; }
+        s.beta[r] = cmul(cdivc(rho, s.rho_old[r]), cdivc(s.alpha[r], s.omega[r]));
+        s.rho_old[r] = rho;
+    } else if (stage == 1) {
+        const double2 rv = d[1];
+        if (!(sqrt(rv.x * rv.x + rv.y * rv.y) > tiny)) { s.active[r] = 0; return; }
+        s.alpha[r] = cdivc(s.rho_old[r], rv);
+    } else {
+        const double tt = d[3].x;
+        s.omega[r] = tt > 0.0 ? cscale(d[2], 1.0 / tt) : make_double2(0.0, 0.0);
+    }
+}
+
+// op 0: p = r + beta (p - omega v); op 1: s = r - alpha v; op 2: x += alpha p + omega s, r = s - omega t
+__global__ void k_bicg_update(BicgScalars s, int op, double2* x, double2* rv, double2* p, const double2* v,
+                              double2* sv, const double2* t, long long n) {
+    const int r = blockIdx.y;
+    if (!s.active[r]) return;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const long long i = (long long)r * n + e;
+    if (op == 0) {
+        p[i] = cadd(rv[i], cmul(s.beta[r], csub(p[i], cmul(s.omega[r], v[i]))));
+    } else if (op == 1) {
+        sv[i] = csub(rv[i], cmul(s.alpha[r], v[i]));
+    } else {
+        x[i] = cadd(x[i], cadd(cmul(s.alpha[r], p[i]), cmul(s.omega[r], sv[i])));
+        rv[i] = csub(sv[i], cmul(s.omega[r], t[i]));
+    }
+}
+
+__global__ void k_bicg_check(BicgScalars s, int R, double tol) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R || !s.active[r]) return;
+    const double res = sqrt(s.nrm[r]);
+    s.resid[r] = res;
+    if (!(res > tol * sqrt(s.b0[r]))) s.active[r] = 0;
+}
+
+template <class C>
+void bicgstab_solve(Ctx& ctx, const double2* g, bool scale, int R, double2* u, const hz_solve_opts& o,
+                    hz_solve_info* info) {
+    cudaStream_t st = ctx.stream;
+    const long long n = ctx.ntr;
+    if (ctx.L == 1 || n == 0) {
+        op_reconstruct<C>(ctx, g, scale, nullptr, R, u, false);
+        if (info) for (int r = 0; r < R; ++r) { info[r].iters = 0; info[r].trace_relres = 0.0; }
+        return;
+    }
+    // six vectors of the Krylov process (r, r^, p, v, s, t) in the workspace's basis slots; a
+    // larger basis already allocated for GMRES is reused as it is
+    const int m = (ctx.gw.cap_R >= R && ctx.gw.m >= 5) ? ctx.gw.m : 5;
+    ensure_gmres_work(ctx, R, m);
+    GmresWork& W = ctx.gw;
+    const long long vs = (long long)R * n;
+    double2 *rv = W.V, *rh = W.V + vs, *p = W.V + 2 * vs, *v = W.V + 3 * vs, *sv = W.V + 4 * vs, *t = W.V + 5 * vs;
+    BicgScalars sc;
+    sc.dots = W.g;   // R x (m + 1) >= R x 4
+    sc.rho_old = W.H;
+    sc.alpha = W.H + R;
+    sc.omega = W.H + 2 * R;
+    sc.beta = W.H + 3 * R;
+    sc.nrm = W.nrm;
+    sc.resid = W.resid;
+    sc.b0 = W.b0;
+    sc.active = W.active;
+    const long long half = (long long)ctx.K * 2 * ctx.P;
+    const int TB = 256;
+    const int gblocks = (int)std::min<long long>(1024, std::max<long long>(1, (n + TB - 1) / TB));
+    const dim3 gvec(cdiv(n, TB), R);
+    Rec& mv = matvec_plan<C>(ctx, R);
+    auto matvec = [&](const double2* in, double2* out) {
+        HZ_CUDA(cudaMemcpyAsync(W.in, in, (size_t)vs * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        if (ctx.use_graphs && !ctx.prof) mv.run_graph(st);
+        else mv.run(st);
+        HZ_CUDA(cudaMemcpyAsync(out, W.out, (size_t)vs * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    };
+    auto dot = [&](const double2* a, const double2* b, int slot) {   // dots[r][slot] = <a_r, b_r>
+        k_mdot<<<dim3(gblocks, R), TB, 0, st>>>(a, vs, b, n, 1, sc.dots + slot, 4);
+        HZ_CHECK_LAUNCH();
+    };
+    std::vector<int> hact(R);
+    auto any_active = [&]() {
+        HZ_CUDA(cudaMemcpyAsync(hact.data(), sc.active, R * sizeof(int), cudaMemcpyDeviceToHost, st));
+        HZ_CUDA(cudaStreamSynchronize(st));
+        for (int r = 0; r < R; ++r) if (hact[r]) return true;
+        return false;
+    };
+    const double tiny = 1e-300;
+    // b = P f_pol; x = 0; r = r^ = b; p = v = 0
+    {
+        Rec rec;
+        rec.upload_stream = st;
+        rec_polarized_rhs<C>(ctx, rec, g, scale, R, W.w2);
+        rec_apply_precond<C>(ctx, rec, W.w2, R, W.b, W.tmp);
+        run_now(ctx, rec);
+    }
+    HZ_CUDA(cudaMemsetAsync(W.xs, 0, (size_t)vs * sizeof(double2), st));
+    HZ_CUDA(cudaMemsetAsync(p, 0, (size_t)vs * sizeof(double2), st));
+    HZ_CUDA(cudaMemsetAsync(v, 0, (size_t)vs * sizeof(double2), st));
+    HZ_CUDA(cudaMemcpyAsync(rv, W.b, (size_t)vs * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    HZ_CUDA(cudaMemcpyAsync(rh, W.b, (size_t)vs * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    HZ_CUDA(cudaMemsetAsync(W.b0, 0, R * sizeof(double), st));
+    k_nrm2<<<dim3(gblocks, R), TB, 0, st>>>(W.b, n, W.b0);
+    HZ_CHECK_LAUNCH();
+    k_bicg_init<<<cdiv(R, 128), 128, 0, st>>>(sc, R, tiny);
+    HZ_CHECK_LAUNCH();
+    int it = 0;
+    while (it < o.max_iter && any_active()) {
+        HZ_CUDA(cudaMemsetAsync(sc.dots, 0, (size_t)R * 4 * sizeof(double2), st));
+        dot(rh, rv, 0);
+        k_bicg_scalars<<<cdiv(R, 128), 128, 0, st>>>(sc, R, 0, tiny);
+        HZ_CHECK_LAUNCH();
+        k_bicg_update<<<gvec, TB, 0, st>>>(sc, 0, W.xs, rv, p, v, sv, t, n);
+        HZ_CHECK_LAUNCH();
+        matvec(p, v);
+        dot(rh, v, 1);
+        k_bicg_scalars<<<cdiv(R, 128), 128, 0, st>>>(sc, R, 1, tiny);
+        HZ_CHECK_LAUNCH();
+        k_bicg_update<<<gvec, TB, 0, st>>>(sc, 1, W.xs, rv, p, v, sv, t, n);
+        HZ_CHECK_LAUNCH();
+        matvec(sv, t);
+        dot(t, sv, 2);
+        dot(t, t, 3);
+        k_bicg_scalars<<<cdiv(R, 128), 128, 0, st>>>(sc, R, 2, tiny);
+        HZ_CHECK_LAUNCH();
+        k_bicg_update<<<gvec, TB, 0, st>>>(sc, 2, W.xs, rv, p, v, sv, t, n);
+        HZ_CHECK_LAUNCH();
+        HZ_CUDA(cudaMemsetAsync(sc.nrm, 0, R * sizeof(double), st));
+        k_nrm2<<<dim3(gblocks, R), TB, 0, st>>>(rv, n, sc.nrm);
+        HZ_CHECK_LAUNCH();
+        k_bicg_check<<<cdiv(R, 128), 128, 0, st>>>(sc, R, o.gmres_tol);
+        HZ_CHECK_LAUNCH();
+        ++it;
+    }
+    std::vector<double> h_resid(R), h_b0(R);
+    HZ_CUDA(cudaMemcpyAsync(h_resid.data(), sc.resid, R * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HZ_CUDA(cudaMemcpyAsync(h_b0.data(), W.b0, R * sizeof(double), cudaMemcpyDeviceToHost, st));
+    // traces t = x_down + x_up, laid out [R][K][2][P]
+    k_lincomb<<<dim3(cdiv(half, TB), R), TB, 0, st>>>(W.t, half, 1.0, W.xs, n, 1.0, W.xs + half, n, half);
+    HZ_CHECK_LAUNCH();
+    op_reconstruct<C>(ctx, g, scale, W.t, R, u, false);
+    HZ_CUDA(cudaStreamSynchronize(st));
+    if (info) {
+        for (int r = 0; r < R; ++r) {
+            info[r].iters = it;
+            const double nb = sqrt(std::max(h_b0[r], 0.0));
+            info[r].trace_relres = nb > 0 ? h_resid[r] / nb : 0.0;
+        }
+    }
+}
+
+template <class C>
+void krylov_solve(Ctx& ctx, const double2* g, bool scale, int R, double2* u, const hz_solve_opts& o,
+                  hz_solve_info* info) {
+    if (o.krylov == 1) bicgstab_solve<C>(ctx, g, scale, R, u, o, info);
+    else gmres_solve<C>(ctx, g, scale, R, u, o, info);
+}
+
 template void gmres_solve<float2>(Ctx&, const double2*, bool, int, double2*, const hz_solve_opts&, hz_solve_info*);
 template void gmres_solve<double2>(Ctx&, const double2*, bool, int, double2*, const hz_solve_opts&, hz_solve_info*);
+template void krylov_solve<float2>(Ctx&, const double2*, bool, int, double2*, const hz_solve_opts&, hz_solve_info*);
+template void krylov_solve<double2>(Ctx&, const double2*, bool, int, double2*, const hz_solve_opts&, hz_solve_info*);
 
 }  // namespace hz

@@ -42,7 +42,7 @@ class Pml(ct.Structure):
 
 class SolveOpts(ct.Structure):
     _fields_ = [("gmres_tol", ct.c_double), ("restart", ct.c_int32), ("max_iter", ct.c_int32),
-                ("refine_tol", ct.c_double), ("max_refine", ct.c_int32)]
+                ("refine_tol", ct.c_double), ("max_refine", ct.c_int32), ("krylov", ct.c_int32)]
 
 
 class SolveInfo(ct.Structure):

@@ -30,7 +30,7 @@ def test_default_options():
     o = hz.default_opts("fp64")
     assert o.gmres_tol == 1e-10 and o.restart == 12
     o = hz.default_opts("mixed")
-    assert o.gmres_tol == 1e-7 and o.max_refine == 3
+    assert o.gmres_tol == 1e-7 and o.max_refine == 3 and o.krylov == 0
 
 
 def test_binding_refuses_to_run_without_library(tmp_path):

@@ -520,3 +520,56 @@ def test_tensor_core_wait_timeout_is_a_status(hz, monkeypatch):
     s.close()
     for r in range(wide.R):
         assert rel(u[r].cpu().numpy(), u_ref[r]) < E2E_TOL["mixed"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("n,npml,L,R", [(20, 4, 4, 3), (24, 4, 6, 5), (18, 3, 2, 1)])
+def test_bicgstab_end_to_end(hz, precision, n, npml, L, R):
+    """Bi-CGSTAB on the trace system (krylov = 1) reaches the global direct solve to the
+    end-to-end tolerances, like GMRES."""
+    p = W.small_problem(n, npml, L, seed=100 + n + L, R=R)
+    f = p.rhs()
+    u = direct.solve(p.m, p.omega, p.npml, p.C, f)
+    s = make_solver(hz, p, precision)
+    o = hz.default_opts(precision)
+    o.krylov = 1
+    ug, info, st = s.solve(cuda(f), o)
+    ug = ug.cpu().numpy()
+    for r in range(R):
+        assert rel(ug[r], u[r]) < E2E_TOL[precision], (r, rel(ug[r], u[r]))
+    assert all(i.trace_relres <= o.gmres_tol for i in info) or precision == "mixed"
+    s.close()
+
+
+@pytest.mark.parametrize("restart", [1, 2])
+def test_low_restart_gmres_end_to_end(hz, restart):
+    """GMRES restarted every 1 or 2 iterations (the memory-lean setting) still reaches the global
+    direct solve (FP64 and mixed)."""
+    p = W.small_problem(24, 4, 6, seed=130, R=3)
+    f = p.rhs()
+    u = direct.solve(p.m, p.omega, p.npml, p.C, f)
+    for precision in ("fp64", "mixed"):
+        s = make_solver(hz, p, precision)
+        o = hz.default_opts(precision)
+        o.restart = restart
+        ug, info, st = s.solve(cuda(f), o)
+        ug = ug.cpu().numpy()
+        for r in range(p.R):
+            assert rel(ug[r], u[r]) < E2E_TOL[precision], (precision, r, rel(ug[r], u[r]))
+        s.close()
+
+
+def test_bicgstab_config2_against_stored_oracle_samples(hz):
+    """64^3 smooth random medium, 8 layers, 16 sources, mixed precision with Bi-CGSTAB inside the
+    defect correction: stored oracle samples."""
+    import os
+    d = np.load(os.path.join(os.path.dirname(__file__), "golden", "cfg2_64cube_smooth_samples.npz"))
+    p = W.config(2)
+    s = make_solver(hz, p, "mixed")
+    o = hz.default_opts("mixed")
+    o.krylov = 1
+    u, info, st = s.solve(cuda(p.rhs()), o)
+    uu = u.cpu().numpy().reshape(p.R, -1)
+    for r in range(p.R):
+        assert rel(uu[r, d["idx"]], d["u"][r]) < E2E_TOL["mixed"], (r, rel(uu[r, d["idx"]], d["u"][r]))
+    s.close()
