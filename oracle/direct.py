@@ -92,10 +92,11 @@ def solve_dense(A: sp.spmatrix, b: np.ndarray) -> np.ndarray:
 
 
 def solve(m: np.ndarray, omega: float, npml: int, C: float, f: np.ndarray,
-          h: float = 1.0, dense: bool = False) -> np.ndarray:
-    """u solving A u = S f for f of shape (R, n, n, n); returns u of the same shape."""
+          h: float = 1.0, dense: bool = False, b: np.ndarray = None) -> np.ndarray:
+    """u solving A u = S f for f of shape (R, n, n, n); returns u of the same shape (b: nodal
+    coefficient of div(b grad u), None for constant density)."""
     n = m.shape[0]
-    A = disc.global_operator(m, omega, npml, C, h)
+    A = disc.global_operator(m, omega, npml, C, h, b=b)
     S = disc.row_scaling(n, npml, C, omega, h)
     B = (S[None] * f).reshape(f.shape[0], -1).T
     if dense:

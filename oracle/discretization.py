@@ -37,6 +37,8 @@ __all__ = [
     "local_z_sigma",
     "local_operator",
     "local_m",
+    "local_b",
+    "half_node_average",
 ]
 
 
@@ -67,13 +69,28 @@ def global_profiles(n: int, npml: int, C: float, omega: float, h: float = 1.0):
             stretch(sigma_global(xh, n, npml, C, h), omega))
 
 
-def assemble(m: np.ndarray, omega: float, prof_x, prof_y, prof_z, h: float = 1.0) -> sp.csr_matrix:
+def half_node_average(b: np.ndarray, axis: int) -> np.ndarray:
+    """Values of a nodal field at the half nodes along one axis: entry i sits at i - 1/2 (n + 1
+    entries), the average of the two nodes around it; beyond the grid the nearest node stands in."""
+    b = np.asarray(b, dtype=np.float64)
+    lo = np.take(b, [0], axis=axis)
+    hi = np.take(b, [b.shape[axis] - 1], axis=axis)
+    ext = np.concatenate([lo, b, hi], axis=axis)
+    n = b.shape[axis]
+    return 0.5 * (np.take(ext, np.arange(n + 1), axis=axis) + np.take(ext, np.arange(1, n + 2), axis=axis))
+
+
+def assemble(m: np.ndarray, omega: float, prof_x, prof_y, prof_z, h: float = 1.0,
+             b: np.ndarray = None) -> sp.csr_matrix:
     """Assemble the symmetric-form 7-point operator on a box (nz, ny, nx), x fastest.
 
     prof_a = (s_node[n_a], s_half[n_a + 1]).  Row (k,j,i):
-      off-diagonal to (k,j,i+-1):  s_y(j) s_z(k) / s_x(i +- 1/2) / h^2   (same for y, z)
+      off-diagonal to (k,j,i+-1):  b(k,j,i+-1/2) s_y(j) s_z(k) / s_x(i +- 1/2) / h^2   (same for y, z)
       diagonal: omega^2 m s_x s_y s_z - (sum of the six couplings, including those
                 that reach beyond the grid, whose neighbours are zero).
+    b is the nodal coefficient of the divergence-form operator div(b grad u) (b = 1/rho for a
+    variable density; None: b = 1, the constant-density Laplacian of Eq. 1), taken at the half
+    nodes as the average of its two nodes (half_node_average).
     """
     nz, ny, nx = m.shape
     sxn, sxh = prof_x
@@ -93,6 +110,12 @@ def assemble(m: np.ndarray, omega: float, prof_x, prof_y, prof_z, h: float = 1.0
     cyp = sxn[X] * szn[Z] / syh[Y + 1] * inv_h2
     czm = sxn[X] * syn[Y] / szh[Z] * inv_h2
     czp = sxn[X] * syn[Y] / szh[Z + 1] * inv_h2
+    if b is not None:
+        assert b.shape == m.shape
+        bx, by, bz = half_node_average(b, 2), half_node_average(b, 1), half_node_average(b, 0)
+        cxm, cxp = cxm * bx[Z, Y, X], cxp * bx[Z, Y, X + 1]
+        cym, cyp = cym * by[Z, Y, X], cyp * by[Z, Y + 1, X]
+        czm, czp = czm * bz[Z, Y, X], czp * bz[Z + 1, Y, X]
     diag = omega ** 2 * m * sxn[X] * syn[Y] * szn[Z] - (cxm + cxp + cym + cyp + czm + czp)
     rows = [gid.ravel()]
     cols = [gid.ravel()]
@@ -115,12 +138,14 @@ def assemble(m: np.ndarray, omega: float, prof_x, prof_y, prof_z, h: float = 1.0
     return A
 
 
-def global_operator(m: np.ndarray, omega: float, npml: int, C: float, h: float = 1.0) -> sp.csr_matrix:
-    """Global discrete operator H of Eq. 7 (symmetric form) on the full n^3 grid."""
+def global_operator(m: np.ndarray, omega: float, npml: int, C: float, h: float = 1.0,
+                    b: np.ndarray = None) -> sp.csr_matrix:
+    """Global discrete operator H of Eq. 7 (symmetric form) on the full n^3 grid (b: nodal
+    coefficient of div(b grad u), None for the constant-density Laplacian)."""
     n = m.shape[0]
     assert m.shape == (n, n, n)
     p = global_profiles(n, npml, C, omega, h)
-    return assemble(m, omega, p, p, p, h)
+    return assemble(m, omega, p, p, p, h, b=b)
 
 
 def row_scaling(n: int, npml: int, C: float, omega: float, h: float = 1.0) -> np.ndarray:
@@ -198,8 +223,19 @@ def local_m(m: np.ndarray, ell: int, parts, npml_local: int) -> np.ndarray:
     return m[zz]
 
 
+def local_b(b: np.ndarray, ell: int, parts, npml_local: int) -> np.ndarray:
+    """b on layer ell's local grid: the owned planes and the one plane beyond each internal
+    interface as they are globally (so that the half-node couplings of the owned rows are the
+    global ones), copied further into the pads."""
+    n = b.shape[0]
+    zlo, zhi = local_grid(ell, parts, n, npml_local)
+    lo, hi = parts[ell]
+    zz = np.clip(np.arange(zlo, zhi + 1), max(lo - 1, 0), min(hi + 1, n - 1))
+    return b[zz]
+
+
 def local_operator(m: np.ndarray, omega: float, ell: int, parts, npml: int, npml_local: int,
-                   C: float, h: float = 1.0) -> sp.csr_matrix:
+                   C: float, h: float = 1.0, b: np.ndarray = None) -> sp.csr_matrix:
     """Local operator H^ell of Eq. 8 on the extended layer (x/y PML inherited)."""
     n = m.shape[0]
     zlo, zhi = local_grid(ell, parts, n, npml_local)
@@ -208,4 +244,5 @@ def local_operator(m: np.ndarray, omega: float, ell: int, parts, npml: int, npml
     zh = np.arange(zlo, zhi + 2, dtype=np.float64) - 0.5
     pz = (stretch(local_z_sigma(zn, ell, parts, n, npml, npml_local, C, h), omega),
           stretch(local_z_sigma(zh, ell, parts, n, npml, npml_local, C, h), omega))
-    return assemble(local_m(m, ell, parts, npml_local), omega, px, px, pz, h)
+    lb = None if b is None else local_b(b, ell, parts, npml_local)
+    return assemble(local_m(m, ell, parts, npml_local), omega, px, px, pz, h, b=lb)

@@ -50,22 +50,23 @@ __all__ = ["PolarizedModel"]
 class PolarizedModel:
     """Algorithm 1 at construction; the online blocks as methods."""
 
-    def __init__(self, m, omega, npml, C, L, npml_local=None, h=1.0):
+    def __init__(self, m, omega, npml, C, L, npml_local=None, h=1.0, b=None):
         self.m = np.asarray(m, dtype=np.float64)
         self.n = n = self.m.shape[0]
         self.omega, self.npml, self.C, self.L, self.h = omega, npml, C, L, h
         self.npml_local = npml if npml_local is None else npml_local
         self.parts = disc.layer_partition(n, npml, L)
         self.K = L - 1
+        self.b = None if b is None else np.asarray(b, dtype=np.float64)
         s, _ = disc.global_profiles(n, npml, C, omega, h)
-        self.c = (s[None, :] * s[:, None]) / (h * h)  # c[y, x] = s_y(y) s_x(x) / h^2
+        self.c0 = (s[None, :] * s[:, None]) / (h * h)  # s_y(y) s_x(x) / h^2
         self.S = disc.row_scaling(n, npml, C, omega, h)
         self.grids = []
         self.solvers = []
         # Algorithm 1: build and factor every local operator
         for ell in range(L):
             zlo, zhi = disc.local_grid(ell, self.parts, n, self.npml_local)
-            H = disc.local_operator(self.m, omega, ell, self.parts, npml, self.npml_local, C, h)
+            H = disc.local_operator(self.m, omega, ell, self.parts, npml, self.npml_local, C, h, b=self.b)
             self.grids.append((zlo, zhi))
             self.solvers.append(GlobalSolver(H, (zhi - zlo + 1, n, n)))
 
@@ -89,13 +90,21 @@ class PolarizedModel:
     def add_plane(self, ell, g, z, v):
         g[z - self.grids[ell][0]] += v
 
+    def coupling(self, P):
+        """c = A[(Q,y,x),(P,y,x)] across the physical half plane between planes P and Q = P+1:
+        s_y s_x / h^2, times b at that half plane for a variable density."""
+        if self.b is None:
+            return self.c0
+        return self.c0 * 0.5 * (self.b[P] + self.b[P + 1])
+
     def S_top(self, ell, pair, g=None):
         """Interface source of interface ell-1 acting on layer ell (ell >= 1)."""
         g = self.zeros_local(ell) if g is None else g
         P = self.parts[ell - 1][1]
         Q = P + 1
-        self.add_plane(ell, g, Q, -self.c * pair[0])
-        self.add_plane(ell, g, P, self.c * pair[1])
+        c = self.coupling(P)
+        self.add_plane(ell, g, Q, -c * pair[0])
+        self.add_plane(ell, g, P, c * pair[1])
         return g
 
     def S_bot(self, ell, pair, g=None):
@@ -103,8 +112,9 @@ class PolarizedModel:
         g = self.zeros_local(ell) if g is None else g
         P = self.parts[ell][1]
         Q = P + 1
-        self.add_plane(ell, g, P, -self.c * pair[1])
-        self.add_plane(ell, g, Q, self.c * pair[0])
+        c = self.coupling(P)
+        self.add_plane(ell, g, P, -c * pair[1])
+        self.add_plane(ell, g, Q, c * pair[0])
         return g
 
     def read_bot(self, ell, w):

@@ -29,6 +29,7 @@ __all__ = [
     "medium_smooth_random",
     "medium_layered_block",
     "point_sources_plane_grid",
+    "density_smooth_random",
     "config",
     "CONFIG_NAMES",
 ]
@@ -137,6 +138,21 @@ def medium_layered_block(n: int, npml: int, n_vlayers: int = 6,
     zsel = (kl >= 2) & (kl <= 4)
     c[np.ix_(zsel, inb, inb)] = c_block
     return 1.0 / (c * c)
+
+
+def density_smooth_random(n: int, seed: int, corr: float = 6.0, rho_min: float = 1.0,
+                          rho_max: float = 2.5) -> np.ndarray:
+    """Smooth random mass density: white noise, Gaussian low-pass, affine map to [rho_min, rho_max]
+    (the recipe of ``medium_smooth_random``).  Returns b = 1/rho, the coefficient of
+    div(b grad u) in the variable-density acoustic operator."""
+    rng = np.random.default_rng(seed)
+    w = rng.standard_normal((n, n, n))
+    k = np.fft.fftfreq(n) * n
+    dz, dy, dx = np.meshgrid(k, k, k, indexing="ij")
+    ker = np.exp(-(dx * dx + dy * dy + dz * dz) / (corr * corr))
+    s = np.real(np.fft.ifftn(np.fft.fftn(w) * np.fft.fftn(ker)))
+    s = (s - s.min()) / (s.max() - s.min())
+    return 1.0 / (rho_min + (rho_max - rho_min) * s)
 
 
 def point_sources_plane_grid(n: int, npml: int, z: int, nsx: int, nsy: int) -> np.ndarray:
