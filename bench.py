@@ -99,28 +99,39 @@ class ClockSampler:
 GOLDEN_CFG3 = os.path.join(ROOT, "tests", "golden", "cfg3_128cube_layered_block.npz")
 
 
-def oracle_error(u, cols):
-    """Relative L2 error of solutions u (R x N complex128 CUDA tensor of the 128^3 workload's
-    sources `cols`) against the stored oracle values (tests/golden, written by the oracle's
-    multifrontal direct solve): over 512 sampled points, and over the full grid estimated from
-    16 sketches <w_k, u> with seeded complex Gaussian w_k.  Max over the right-hand sides."""
+GOLDEN = {3: GOLDEN_CFG3,
+          2: os.path.join(ROOT, "tests", "golden", "cfg2_64cube_smooth_samples.npz"),
+          "2d": os.path.join(ROOT, "tests", "golden", "cfg2_64cube_density_samples.npz")}
+
+
+def oracle_error(u, cols, key=3):
+    """Relative L2 error of solutions u (R x N complex128 CUDA tensor of a workload's sources
+    `cols`) against the stored oracle values (tests/golden, written by scripts that call only the
+    oracle): over the sampled points, and (128^3) over the full grid estimated from 16 sketches
+    <w_k, u> with seeded complex Gaussian w_k.  Max over the right-hand sides."""
     import torch
-    if not os.path.exists(GOLDEN_CFG3):
+    path = GOLDEN.get(key)
+    if not path or not os.path.exists(path):
         return None
-    ref = np.load(GOLDEN_CFG3)
+    ref = np.load(path)
     idx = torch.from_numpy(ref["idx"]).to(u.device)
     s_ref = ref["u"][cols]
     samp = u[:, idx].cpu().numpy()
     e_s = np.linalg.norm(samp - s_ref, axis=1) / np.linalg.norm(s_ref, axis=1)
-    N, K, seed = u.shape[1], int(ref["sketch_k"]), int(ref["sketch_seed"])
-    sk = np.zeros((u.shape[0], K), dtype=np.complex128)
-    for k in range(K):
-        g = np.random.default_rng(seed + k).standard_normal(2 * N)
-        w = torch.from_numpy((g[:N] + 1j * g[N:]) / np.sqrt(2.0)).to(u.device)
-        sk[:, k] = (u @ w).cpu().numpy()
-    e_f = np.sqrt(np.mean(np.abs(sk - ref["sketch"][cols]) ** 2, axis=1)) / ref["norms"][cols]
-    return {"max_rel_err_samples": float(e_s.max()), "max_rel_err_full_grid_sketch": float(e_f.max()),
-            "R": int(len(cols)), "reference": "multifrontal FP64 global direct solve (stored samples/sketches)"}
+    out = {"max_rel_err_samples": float(e_s.max()), "R": int(len(cols)), "samples": int(idx.numel())}
+    if "sketch" in ref:
+        N, K, seed = u.shape[1], int(ref["sketch_k"]), int(ref["sketch_seed"])
+        sk = np.zeros((u.shape[0], K), dtype=np.complex128)
+        for k in range(K):
+            g = np.random.default_rng(seed + k).standard_normal(2 * N)
+            w = torch.from_numpy((g[:N] + 1j * g[N:]) / np.sqrt(2.0)).to(u.device)
+            sk[:, k] = (u @ w).cpu().numpy()
+        e_f = np.sqrt(np.mean(np.abs(sk - ref["sketch"][cols]) ** 2, axis=1)) / ref["norms"][cols]
+        out["max_rel_err_full_grid_sketch"] = float(e_f.max())
+        out["reference"] = "multifrontal FP64 global direct solve (stored samples/sketches)"
+    else:
+        out["reference"] = "SuperLU FP64 global direct solve (stored samples)"
+    return out
 
 
 def measured_traffic(kernel, config, R):
@@ -219,9 +230,14 @@ def run_ours(args):
     src = p.sources[:R]
     n = p.n
     N3 = n ** 3
+    # second workload: the same medium with a seeded smooth random density (div(b grad u), b = 1/rho)
+    bden = W.density_smooth_random(n, seed=1801 + 22) if args.density else None
+    gkey = (str(args.config) + "d") if args.density else args.config
+    if args.density and args.config != 2:
+        raise SystemExit("--density: the variable-density workload is the 64^3 one (--config 2)")
 
     # ---------------- mixed-precision solver (the measured path)
-    s = hz.Solver(p.m, p.omega, p.npml, p.C, p.n_layers, precision="mixed", stream=stream)
+    s = hz.Solver(p.m, p.omega, p.npml, p.C, p.n_layers, precision="mixed", stream=stream, b=bden)
     t0 = time.perf_counter()
     s.factor()
     factor_s = time.perf_counter() - t0
@@ -358,8 +374,8 @@ def run_ours(args):
 
     # ---------------- error of the headline solve against the stored oracle values
     oracle_err = None
-    if args.config == 3 and R == p.R:
-        oracle_err = oracle_error(u.reshape(R, N3), np.arange(R))
+    if R == p.R:
+        oracle_err = oracle_error(u.reshape(R, N3), np.arange(R), gkey)
 
     # ---------------- FP64 GPU path on the same sources, same GMRES tolerance (like for like),
     # with the mixed path timed on the same number of sources
@@ -378,7 +394,7 @@ def run_ours(args):
         s.close()
         del s
         torch.cuda.empty_cache()
-        s64 = hz.Solver(p.m, p.omega, p.npml, p.C, p.n_layers, precision="fp64", stream=stream)
+        s64 = hz.Solver(p.m, p.omega, p.npml, p.C, p.n_layers, precision="fp64", stream=stream, b=bden)
         t0 = time.perf_counter()
         s64.factor()
         f64_s = time.perf_counter() - t0
@@ -397,9 +413,9 @@ def run_ours(args):
                 "mixed_same_R_value": R64 / (ms_mixed / 1e3),
                 "mixed_vs_fp64_speedup_same_R": ms64 / ms_mixed,
                 "mixed_vs_fp64_rel_diff": diff}
-        if args.config == 3 and R == p.R:
-            fp64["oracle_error"] = oracle_error(u64.reshape(R64, N3), np.arange(R64))
-            fp64["mixed_oracle_error_same_R"] = oracle_error(u_mixed.reshape(R64, N3), np.arange(R64))
+        if R == p.R:
+            fp64["oracle_error"] = oracle_error(u64.reshape(R64, N3), np.arange(R64), gkey)
+            fp64["mixed_oracle_error_same_R"] = oracle_error(u_mixed.reshape(R64, N3), np.arange(R64), gkey)
         s64.close()
     else:
         s.close()
@@ -428,7 +444,8 @@ def run_ours(args):
             "config": {"workload": (f"128^3 layered+block medium, PML 10, 16 layers, R={R} point sources, "
                                     "mixed precision (complex64 local solves, FP64 GMRES + defect correction)")
                        if args.config == 3 else
-                       (f"{W.CONFIG_NAMES[args.config]} (solved with R={R}), mixed precision"),
+                       (f"{W.CONFIG_NAMES[args.config]}{' with smooth random density 1..2.5' if args.density else ''} "
+                        f"(solved with R={R}), mixed precision"),
                        "n": n, "layers": p.n_layers, "R": R, "precision": "mixed",
                        "l2": "inputs larger than L2: ~40 GB of factors streamed every GMRES iteration",
                        "precond_tf32_terms": 1 if os.environ.get("HZ_PRECOND_SPLIT", "3") == "1" else 3,
@@ -586,6 +603,8 @@ def main():
                     help="print the per-phase, per-level substitution profile of the profiled solve (stderr)")
     ap.add_argument("--gmres-tol", type=float, default=1e-5)
     ap.add_argument("--refine-tol", type=float, default=1e-6)
+    ap.add_argument("--density", action="store_true",
+                    help="variable-density workload (64^3 medium with a smooth random density, --config 2)")
     ap.add_argument("--krylov", default="gmres", choices=["gmres", "bicgstab"],
                     help="Krylov solver on the trace system (hz_solve_opts.krylov)")
     args = ap.parse_args()

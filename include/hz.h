@@ -128,6 +128,19 @@ hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz
                     int32_t n_layers, hz_precision prec, void* stream, hz_handle** out);
 
 /*
+ * hz_create_ex -- hz_create for a heterogeneous density (the extension the paper's Introduction
+ * names): the operator is div(b grad u) + omega^2 m u with b = 1/rho, discretized in the same
+ * symmetric 7-point form with b at the half nodes (the average of the two nodes; the node itself
+ * beyond the grid), so the structure, the method and the boundary are unchanged.
+ *   b   1/rho, nz*ny*nx doubles, host memory, every entry finite and > 0; copied.  NULL gives
+ *       b = 1 (exactly hz_create)
+ * Other arguments and errors as hz_create, plus HZ_ERR_ARG for b <= 0 and HZ_ERR_NONFINITE for
+ * a non-finite b.
+ */
+hz_status hz_create_ex(const hz_grid* grid, const double* m, const double* b, double omega, const hz_pml* pml,
+                       int32_t n_layers, hz_precision prec, void* stream, hz_handle** out);
+
+/*
  * hz_factor -- offline phase (Algorithm 1): assemble and factor every layer's
  * local operator H^l = L D L^T (complex symmetric, unpivoted, nested dissection,
  * FP64 diagonal pivot blocks), keeping the factors resident in device memory.  In mixed

@@ -45,7 +45,8 @@ __device__ inline long long tri_index(int rt, int ct) { return (long long)rt * (
 
 // Stencil coefficient of the local operator for the column unknown `cell` and direction d
 // (0 = diagonal, 1..6 = x-, x+, y-, y+, z-, z+), in FP64: symmetric form of the stretched
-// 7-point operator (s_a at half nodes for the derivative along a, at nodes otherwise).
+// 7-point operator (s_a at half nodes for the derivative along a, at nodes otherwise), times b at
+// the half node for a variable density (div(b grad u), b = 1/rho).
 __device__ double2 stencil_coef(const LayerCoef& lc, int cell, int d) {
     int x = cell % lc.nx;
     int y = (cell / lc.nx) % lc.ny;
@@ -59,6 +60,15 @@ __device__ double2 stencil_coef(const LayerCoef& lc, int cell, int d) {
     c[4] = cscale(cmul(sxz, lc.isy_h[y + 1]), lc.inv_h2);
     c[5] = cscale(cmul(sxy, lc.isz_h[z]), lc.inv_h2);
     c[6] = cscale(cmul(sxy, lc.isz_h[z + 1]), lc.inv_h2);
+    if (lc.b) {   // variable density: b at the half nodes
+        const long long P = (long long)lc.nx * lc.ny;
+        c[1] = cscale(c[1], bhalf(lc.b, cell, x, lc.nx, 1, -1));
+        c[2] = cscale(c[2], bhalf(lc.b, cell, x, lc.nx, 1, +1));
+        c[3] = cscale(c[3], bhalf(lc.b, cell, y, lc.ny, lc.nx, -1));
+        c[4] = cscale(c[4], bhalf(lc.b, cell, y, lc.ny, lc.nx, +1));
+        c[5] = cscale(c[5], bhalf(lc.b, cell, z, lc.nzl, P, -1));
+        c[6] = cscale(c[6], bhalf(lc.b, cell, z, lc.nzl, P, +1));
+    }
     if (d > 0) return c[d];
     double2 dg = cscale(cmul(sxy, sz), lc.omega2 * lc.m[cell]);
     for (int k = 1; k <= 6; ++k) dg = csub(dg, c[k]);

@@ -304,6 +304,11 @@ void hz_default_opts(hz_precision prec, hz_solve_opts* o) {
 
 hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz_pml* pml, int32_t n_layers,
                     hz_precision prec, void* stream, hz_handle** out) {
+    return hz_create_ex(grid, m, nullptr, omega, pml, n_layers, prec, stream, out);
+}
+
+hz_status hz_create_ex(const hz_grid* grid, const double* m, const double* b, double omega, const hz_pml* pml,
+                       int32_t n_layers, hz_precision prec, void* stream, hz_handle** out) {
     if (out) *out = nullptr;
     hz_handle* h = nullptr;
     try {
@@ -319,6 +324,11 @@ hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz
         const long long N3 = (long long)grid->nx * grid->ny * grid->nz;
         for (long long i = 0; i < N3; ++i)
             if (!std::isfinite(m[i])) throw Error{HZ_ERR_NONFINITE, "m has a non-finite entry"};
+        if (b)
+            for (long long i = 0; i < N3; ++i) {
+                if (!std::isfinite(b[i])) throw Error{HZ_ERR_NONFINITE, "b has a non-finite entry"};
+                if (!(b[i] > 0)) throw Error{HZ_ERR_ARG, "b = 1/rho must be positive"};
+            }
         h = new hz_handle();
         Ctx& c = h->ctx;
         c.nx = grid->nx; c.ny = grid->ny; c.nz = grid->nz; c.h = grid->h;
@@ -343,6 +353,7 @@ hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz
         c.d_sy_n = dev_copy(syn); c.d_isy_h = dev_copy(isyh);
         c.d_sz_n = dev_copy(szn); c.d_isz_h = dev_copy(iszh);
         c.d_m = dev_copy(std::vector<double>(m, m + N3));
+        if (b) c.d_b = dev_copy(std::vector<double>(b, b + N3));
         c.d_flag = (int*)dev_alloc(4 * sizeof(int));
         HZ_CUDA(cudaMemset(c.d_flag, 0, 4 * sizeof(int)));
         // layer partition: physical planes split evenly, earlier layers take the remainder;
@@ -406,10 +417,21 @@ hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz
             ly.d_sz_n = dev_copy(lzn);
             ly.d_isz_h = dev_copy(lzh);
             ly.d_m = dev_copy(lm);
+            if (b) {
+                // b on the local grid: the owned planes and the plane beyond each internal interface
+                // as they are globally (the owned rows' half-node couplings are then the global
+                // ones), copied further into the pads
+                std::vector<double> lb((size_t)ly.nzl * c.P);
+                for (int k = 0; k < ly.nzl; ++k) {
+                    int zg = std::min(std::max(ly.zlo + k, std::max(ly.lo - 1, 0)), std::min(ly.hi + 1, nz - 1));
+                    std::memcpy(&lb[(size_t)k * c.P], b + (size_t)zg * c.P, c.P * sizeof(double));
+                }
+                ly.d_b = dev_copy(lb);
+            }
             LayerCoef lc;
             lc.sx_n = c.d_sx_n; lc.isx_h = c.d_isx_h; lc.sy_n = c.d_sy_n; lc.isy_h = c.d_isy_h;
-            lc.sz_n = ly.d_sz_n; lc.isz_h = ly.d_isz_h; lc.m = ly.d_m;
-            lc.nx = c.nx; lc.ny = c.ny; lc.omega2 = omega * omega; lc.inv_h2 = 1.0 / (c.h * c.h);
+            lc.sz_n = ly.d_sz_n; lc.isz_h = ly.d_isz_h; lc.m = ly.d_m; lc.b = ly.d_b;
+            lc.nx = c.nx; lc.ny = c.ny; lc.nzl = ly.nzl; lc.omega2 = omega * omega; lc.inv_h2 = 1.0 / (c.h * c.h);
             coefs.push_back(lc);
             c.layers.push_back(ly);
         }
@@ -535,11 +557,12 @@ hz_status hz_destroy(hz_handle* h) {
             cudaFree(sh.d_nodes); cudaFree(sh.d_pos); cudaFree(sh.d_upd_idx); cudaFree(sh.d_asm); cudaFree(sh.d_emap);
         }
         for (auto& ly : c.layers) {
-            cudaFree(ly.d_sz_n); cudaFree(ly.d_isz_h); cudaFree(ly.d_m); cudaFree(ly.d_fac); cudaFree(ly.d_dinv);
+            cudaFree(ly.d_sz_n); cudaFree(ly.d_isz_h); cudaFree(ly.d_m); cudaFree(ly.d_b); cudaFree(ly.d_fac);
+            cudaFree(ly.d_dinv);
         }
         cudaFree(c.d_coefs);
         cudaFree(c.d_sx_n); cudaFree(c.d_isx_h); cudaFree(c.d_sy_n); cudaFree(c.d_isy_h);
-        cudaFree(c.d_sz_n); cudaFree(c.d_isz_h); cudaFree(c.d_m);
+        cudaFree(c.d_sz_n); cudaFree(c.d_isz_h); cudaFree(c.d_m); cudaFree(c.d_b);
     }
     delete h;
     return HZ_OK;
@@ -564,7 +587,7 @@ hz_status hz_create_shared(hz_handle* src, void* stream, hz_handle** out) {
         c.layers = s.layers;    // factors borrowed
         c.d_coefs = s.d_coefs;
         c.d_sx_n = s.d_sx_n; c.d_isx_h = s.d_isx_h; c.d_sy_n = s.d_sy_n; c.d_isy_h = s.d_isy_h;
-        c.d_sz_n = s.d_sz_n; c.d_isz_h = s.d_isz_h; c.d_m = s.d_m;
+        c.d_sz_n = s.d_sz_n; c.d_isz_h = s.d_isz_h; c.d_m = s.d_m; c.d_b = s.d_b;
         c.tc_mode = s.tc_mode; c.tc_ks = s.tc_ks; c.tc_min_tiles = s.tc_min_tiles; c.precond_split = s.precond_split; c.tc_cfg = s.tc_cfg;
         c.sparse_subst = s.sparse_subst;
         c.tc_wait_polls = s.tc_wait_polls;

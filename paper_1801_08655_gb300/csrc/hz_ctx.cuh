@@ -23,7 +23,8 @@ struct LayerCoef {
     const double2* sz_n;   // local z profile (nzl)
     const double2* isz_h;  // (nzl+1)
     const double* m;       // local m (nzl*ny*nx)
-    int nx, ny;
+    const double* b;       // local b = 1/rho (nzl*ny*nx) or nullptr (constant density)
+    int nx, ny, nzl;
     double omega2, inv_h2;
 };
 
@@ -159,6 +160,7 @@ struct Ctx {
     double2 *d_sx_n = nullptr, *d_isx_h = nullptr, *d_sy_n = nullptr, *d_isy_h = nullptr;
     double2 *d_sz_n = nullptr, *d_isz_h = nullptr;
     double* d_m = nullptr;
+    double* d_b = nullptr;   // b = 1/rho on the global grid, nullptr for constant density
     int* d_flag = nullptr;   // device error flags: [0] tiny pivot
     bool factored = false;
     bool owns_shared = true;  // false for handles that borrow another handle's factors (hz_create_shared)

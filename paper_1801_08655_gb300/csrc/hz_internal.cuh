@@ -55,6 +55,17 @@ template <class C> __host__ __device__ inline C from_d(double2 a);
 template <> __host__ __device__ inline float2 from_d<float2>(double2 a) { return to_f(a); }
 template <> __host__ __device__ inline double2 from_d<double2>(double2 a) { return a; }
 
+// Coefficient b of div(b grad u) (b = 1/rho) at the half node between cell i (coordinate `coord`
+// of `n` along an axis of element stride `stride`) and its neighbour in direction d = -1 / +1:
+// the average of the two nodes, the cell itself standing in for a neighbour beyond the grid.
+// b == nullptr means constant density (b = 1).
+__host__ __device__ inline double bhalf(const double* b, long long i, int coord, int n, long long stride, int d) {
+    if (!b) return 1.0;
+    const int c2 = coord + d;
+    const double v2 = (c2 >= 0 && c2 < n) ? b[i + d * stride] : b[i];
+    return 0.5 * (b[i] + v2);
+}
+
 // ------------------------------------------------------------------------------------------
 // symbolic structures (host), built once per distinct slab shape
 // ------------------------------------------------------------------------------------------
@@ -126,6 +137,9 @@ struct Layer {
     double2* d_sz_n = nullptr;     // s_z at local nodes (nzl)
     double2* d_isz_h = nullptr;    // 1/s_z at local half nodes (nzl+1), index k <-> k - 1/2
     double* d_m = nullptr;         // m on the local grid (nzl*ny*nx)
+    double* d_b = nullptr;         // b = 1/rho on the local grid (owned planes and one plane beyond
+                                   // each internal interface as they are globally, copied further
+                                   // into the pads), or nullptr for constant density
     void* d_fac = nullptr;         // packed factor tiles (complex T)
     void* d_dinv = nullptr;        // D^{-1} by elimination index (complex T, N)
 };

@@ -79,7 +79,7 @@ struct DeviceGuard {
 __global__ void k_residual_static(const double2* f, const double2* u, double2* rout, double* norms, int nx,
                                   int ny, int nz, const double2* sxn, const double2* isxh, const double2* syn,
                                   const double2* isyh, const double2* szn, const double2* iszh, const double* m,
-                                  double omega2, double inv_h2) {
+                                  const double* b, double omega2, double inv_h2) {
     const long long N3 = (long long)nx * ny * nz;
     const int r = blockIdx.y;
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -92,6 +92,12 @@ __global__ void k_residual_static(const double2* f, const double2* u, double2* r
         double2 c1 = cscale(cmul(syz, isxh[x]), inv_h2), c2 = cscale(cmul(syz, isxh[x + 1]), inv_h2);
         double2 c3 = cscale(cmul(sxz, isyh[y]), inv_h2), c4 = cscale(cmul(sxz, isyh[y + 1]), inv_h2);
         double2 c5 = cscale(cmul(sxy, iszh[z]), inv_h2), c6 = cscale(cmul(sxy, iszh[z + 1]), inv_h2);
+        if (b) {   // variable density: b at the half nodes
+            const long long pl_ = (long long)nx * ny;
+            c1 = cscale(c1, bhalf(b, i, x, nx, 1, -1)); c2 = cscale(c2, bhalf(b, i, x, nx, 1, +1));
+            c3 = cscale(c3, bhalf(b, i, y, ny, nx, -1)); c4 = cscale(c4, bhalf(b, i, y, ny, nx, +1));
+            c5 = cscale(c5, bhalf(b, i, z, nz, pl_, -1)); c6 = cscale(c6, bhalf(b, i, z, nz, pl_, +1));
+        }
         double2 dg = cscale(cmul(sxy, sz), omega2 * m[i]);
         dg = csub(dg, cadd(cadd(cadd(c1, c2), cadd(c3, c4)), cadd(c5, c6)));
         double2 au = cmul(dg, ur[i]);
@@ -165,7 +171,7 @@ extern "C" hz_status hz_volume_residual_noalloc(hz_handle* h, const double* rhs,
     dim3 grid((unsigned)((N3 + 255) / 256), (unsigned)R);
     hz::k_residual_static<<<grid, 256, 0, c.stream>>>((const double2*)rhs, (const double2*)u, (double2*)r, scratch,
                                                      c.nx, c.ny, c.nz, c.d_sx_n, c.d_isx_h, c.d_sy_n, c.d_isy_h,
-                                                     c.d_sz_n, c.d_isz_h, c.d_m, c.omega * c.omega,
+                                                     c.d_sz_n, c.d_isz_h, c.d_m, c.d_b, c.omega * c.omega,
                                                      1.0 / (c.h * c.h));
     hz::g_launch_count.fetch_add(1, std::memory_order_relaxed);
     double sums[2 * hz::kNoallocMaxCols];

@@ -45,6 +45,7 @@ template <class C> struct Inject {
     int ldc, col0;
     int zl_m, off_m;         // local plane receiving -c * src[off_m + cell]
     int zl_p, off_p;         // local plane receiving +c * src[off_p + cell]
+    const double* b;         // layer's local b = 1/rho, or nullptr (constant density)
 };
 
 template <class C>
@@ -56,7 +57,10 @@ __global__ void k_inject(const Inject<C>* inj, const double2* sx, const double2*
     const int r = blockIdx.y;
     if (cell >= P) return;
     const int x = cell % nx, y = cell / nx;
-    const double2 c = cscale(cmul(sx[x], sy[y]), inv_h2);
+    // c = A[(Q,y,x),(P,y,x)]: the z-coupling across the physical half plane between the pair's
+    // planes (zl_m and zl_p are the two of them), times b at that half plane
+    double2 c = cscale(cmul(sx[x], sy[y]), inv_h2);
+    if (q.b) c = cscale(c, 0.5 * (q.b[(long long)q.zl_m * P + cell] + q.b[(long long)q.zl_p * P + cell]));
     const double2* s = q.src + (long long)r * q.rstride;
     const double2 vm = cneg(cmul(c, s[q.off_m + cell]));
     const double2 vp = cmul(c, s[q.off_p + cell]);
@@ -163,7 +167,7 @@ __global__ void k_pairs_axpy(double2* y, long long ystride, const double2* x, lo
 __global__ void k_residual(const double2* f, const double2* u, double2* rout, double* norms, int scale,
                            int nx, int ny, int nz, const double2* sxn, const double2* isxh,
                            const double2* syn, const double2* isyh, const double2* szn,
-                           const double2* iszh, const double* m, double omega2, double inv_h2) {
+                           const double2* iszh, const double* m, const double* b, double omega2, double inv_h2) {
     const long long N3 = (long long)nx * ny * nz;
     const int r = blockIdx.y;
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -176,6 +180,12 @@ __global__ void k_residual(const double2* f, const double2* u, double2* rout, do
         double2 c1 = cscale(cmul(syz, isxh[x]), inv_h2), c2 = cscale(cmul(syz, isxh[x + 1]), inv_h2);
         double2 c3 = cscale(cmul(sxz, isyh[y]), inv_h2), c4 = cscale(cmul(sxz, isyh[y + 1]), inv_h2);
         double2 c5 = cscale(cmul(sxy, iszh[z]), inv_h2), c6 = cscale(cmul(sxy, iszh[z + 1]), inv_h2);
+        if (b) {   // variable density: b at the half nodes
+            const long long pl_ = (long long)nx * ny;
+            c1 = cscale(c1, bhalf(b, i, x, nx, 1, -1)); c2 = cscale(c2, bhalf(b, i, x, nx, 1, +1));
+            c3 = cscale(c3, bhalf(b, i, y, ny, nx, -1)); c4 = cscale(c4, bhalf(b, i, y, ny, nx, +1));
+            c5 = cscale(c5, bhalf(b, i, z, nz, pl_, -1)); c6 = cscale(c6, bhalf(b, i, z, nz, pl_, +1));
+        }
         double2 dg = cscale(cmul(sxy, sz), omega2 * m[i]);
         dg = csub(dg, cadd(cadd(cadd(c1, c2), cadd(c3, c4)), cadd(c5, c6)));
         double2 au = cmul(dg, ur[i]);
@@ -470,6 +480,7 @@ Inject<C> make_inject(Ctx& ctx, int l, bool top, const double2* pair, long long 
     q.rstride = rstride;
     q.ldc = ldc;
     q.col0 = col0;
+    q.b = ly.d_b;
     const int Pl = (int)ctx.P;
     if (top) {  // Q_{l-1} = lo gets -c t(P); P_{l-1} = lo-1 gets +c t(Q)
         q.zl_m = ly.lo - ly.zlo; q.off_m = 0;
@@ -828,7 +839,7 @@ void op_volume_residual(Ctx& ctx, const double2* f, bool scale, const double2* u
     dim3 grid(cdiv(N3, 256), R);
     k_residual<<<grid, 256, 0, ctx.stream>>>(f, u, r, norms, scale ? 1 : 0, ctx.nx, ctx.ny, ctx.nz, ctx.d_sx_n,
                                              ctx.d_isx_h, ctx.d_sy_n, ctx.d_isy_h, ctx.d_sz_n, ctx.d_isz_h, ctx.d_m,
-                                             ctx.omega * ctx.omega, 1.0 / (ctx.h * ctx.h));
+                                             ctx.d_b, ctx.omega * ctx.omega, 1.0 / (ctx.h * ctx.h));
     HZ_CHECK_LAUNCH();
 }
 

@@ -24,7 +24,7 @@ STATUS_NAMES = ["HZ_OK", "HZ_ERR_ARG", "HZ_ERR_OOM", "HZ_ERR_ADMISSION", "HZ_ERR
 PREC = {"fp64": 0, "mixed": 1, "mixed64": 2}
 
 EXPORTED = [
-    "hz_default_opts", "hz_create", "hz_factor", "hz_solve", "hz_solve_host", "hz_destroy", "hz_last_error",
+    "hz_default_opts", "hz_create", "hz_create_ex", "hz_factor", "hz_solve", "hz_solve_host", "hz_destroy", "hz_last_error",
     "hz_layer_info", "hz_factor_stats", "hz_layer_solve_cost", "hz_layer_solve", "hz_polarized_rhs",
     "hz_apply_mpol", "hz_apply_precond", "hz_reconstruct", "hz_volume_residual",
     "hz_profile_begin", "hz_profile_begin_detail", "hz_profile_end", "hz_profile_kernel", "hz_profile_report", "hz_kernel_launches", "hz_volume_residual_noalloc",
@@ -71,6 +71,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.hz_default_opts.argtypes = [ct.c_int, P(SolveOpts)]
     lib.hz_default_opts.restype = None
     lib.hz_create.argtypes = [P(Grid), VP, D, P(Pml), I32, ct.c_int, VP, P(VP)]
+    lib.hz_create_ex.argtypes = [P(Grid), VP, VP, D, P(Pml), I32, ct.c_int, VP, P(VP)]
     lib.hz_factor.argtypes = [VP]
     lib.hz_solve.argtypes = [VP, VP, I32, VP, P(SolveOpts), P(SolveInfo)]
     lib.hz_solve_host.argtypes = [VP, VP, I32, VP, P(SolveOpts), P(SolveInfo)]
@@ -124,10 +125,15 @@ class Solver:
     """One (grid, m, omega, PML, layers, precision) problem with resident factors."""
 
     def __init__(self, m: np.ndarray, omega: float, npml: int, C: float, n_layers: int,
-                 precision: str = "mixed", npml_local: int = -1, h: float = 1.0, stream=None):
+                 precision: str = "mixed", npml_local: int = -1, h: float = 1.0, stream=None,
+                 b: Optional[np.ndarray] = None):
+        """b: optional 1/rho on the grid (variable density, hz_create_ex); None for constant density."""
         import torch
         self.lib = load()
         m = np.ascontiguousarray(np.asarray(m, dtype=np.float64))
+        if b is not None:
+            b = np.ascontiguousarray(np.asarray(b, dtype=np.float64))
+            assert b.shape == m.shape
         nz, ny, nx = m.shape
         self.shape = (nz, ny, nx)
         self.precision = precision
@@ -138,8 +144,9 @@ class Solver:
         g = Grid(nx, ny, nz, h)
         p = Pml(npml, C, npml_local)
         hnd = ct.c_void_p()
-        st = self.lib.hz_create(ct.byref(g), m.ctypes.data, omega, ct.byref(p), n_layers, PREC[precision],
-                                ct.c_void_p(self.stream.cuda_stream), ct.byref(hnd))
+        st = self.lib.hz_create_ex(ct.byref(g), m.ctypes.data, b.ctypes.data if b is not None else None, omega,
+                                   ct.byref(p), n_layers, PREC[precision], ct.c_void_p(self.stream.cuda_stream),
+                                   ct.byref(hnd))
         if st != HZ_OK:
             raise HzError(st, self.lib.hz_last_error(None).decode())
         self.h = hnd
