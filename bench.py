@@ -3,8 +3,9 @@
 Workload (one "step" = one pass of the whole online path on one batch): the 128^3
 layered + block medium (PML 10, 16 layers, omega at 8 points per wavelength), R = 128
 point sources on a 16 x 8 grid on the plane z = 12, solved to relative error 1e-5 in mixed
-precision: complex64 factors and local solves, FP64 GMRES on the traces to 1e-5, then FP64
-defect correction until the FP64 volume residual is <= 1e-6.  The factors (about 40 GB) are resident and re-streamed every
+precision: complex64 factors and local solves, FP64 GMRES on the traces to 1e-4, then FP64
+defect correction until the FP64 volume residual is <= 1e-5 (measured error against the stored
+oracle values: ~7e-7, reported in the line).  The factors (about 40 GB) are resident and re-streamed every
 GMRES iteration, so every step reads far more than the 129 MB L2.
 
 Under torchrun (N > 1) every rank solves its own replica (independent problem, no
@@ -399,7 +400,7 @@ def run_ours(args):
         s64.factor()
         f64_s = time.perf_counter() - t0
         opts64 = hz.default_opts("fp64")
-        opts64.gmres_tol = args.gmres_tol
+        opts64.gmres_tol = args.fp64_gmres_tol
         u64 = torch.empty_like(rr)
         e0.record(stream)
         _, inf64, _ = s64.solve(rr, opts64, u=u64, allow_noconv=True)
@@ -601,8 +602,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-levels", action="store_true",
                     help="print the per-phase, per-level substitution profile of the profiled solve (stderr)")
-    ap.add_argument("--gmres-tol", type=float, default=1e-5)
-    ap.add_argument("--refine-tol", type=float, default=1e-6)
+    # accuracy target: relative error <= 1e-5 against the oracle.  One FP64 defect-correction pass
+    # is needed (the complex64 local solves alone leave ~2.4e-4 at 128^3); GMRES to 1e-4 and a
+    # volume residual <= 1e-5 give 7.3e-7 measured against the stored oracle values (the line
+    # reports the measured error as oracle_error)
+    ap.add_argument("--gmres-tol", type=float, default=1e-4)
+    ap.add_argument("--refine-tol", type=float, default=1e-5)
+    ap.add_argument("--fp64-gmres-tol", type=float, default=1e-5,
+                    help="GMRES tolerance of the FP64 comparison (1e-5 gives ~1.2e-6 against the oracle)")
     ap.add_argument("--density", action="store_true",
                     help="variable-density workload (64^3 medium with a smooth random density, --config 2)")
     ap.add_argument("--krylov", default="gmres", choices=["gmres", "bicgstab"],

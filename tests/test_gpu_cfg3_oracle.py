@@ -2,7 +2,7 @@
 
 The workload is the bench's: 128^3 layered + block medium, PML 10, 16 layers, 128 point sources,
 solved in the bench's launch configuration (default autotuning, all 128 right-hand sides in one
-call, GMRES to 1e-5 and FP64 defect correction to a volume residual of 1e-6) in mixed precision,
+call, GMRES to 1e-4 and FP64 defect correction to a volume residual of 1e-5) in mixed precision,
 and 8 of the sources in FP64 mode.  The stored values come from the multifrontal FP64 global
 direct solve of the same discrete system (tests/golden/make_golden_cfg3.py, which calls only
 the oracle):
@@ -68,7 +68,7 @@ def test_config3_headline_against_oracle():
     s = hz.Solver(p.m, p.omega, p.npml, p.C, p.n_layers, precision="mixed")
     s.factor()
     opts = hz.default_opts("mixed")
-    opts.gmres_tol, opts.refine_tol = 1e-5, 1e-6
+    opts.gmres_tol, opts.refine_tol = 1e-4, 1e-5    # the bench's defaults
     u, info, _ = s.solve(rhs, opts)
     s.close()
     del s
