@@ -545,15 +545,24 @@ def run_serving(args):
     opts.restart = 6
     rec = W.point_sources_plane_grid(n, p, p + 2, 8, 8)
     recv = (rec[:, 0] * n + rec[:, 1]) * n + rec[:, 2]
+    t_start = time.perf_counter()
+
+    def log(msg):
+        print(f"[{time.perf_counter() - t_start:8.1f} s] {msg}", file=sys.stderr, flush=True)
+
     t0 = time.perf_counter()
     srv = serving.Server(m, omegas, p, W.pml_constant(4.5), L, npml_local=args.npml_local, precision="mixed",
-                         max_cols=args.max_cols, max_workers=2, opts=opts, receivers=recv)
+                         max_cols=args.max_cols, max_workers=2, opts=opts, receivers=recv, log=log)
     factor_s = time.perf_counter() - t0
-    # calibrate the saturated throughput with one full batch at the middle frequency
+    log(f"factored {len(omegas)} frequencies in {factor_s:.1f} s")
+    # calibrate the saturated throughput: full batches at every frequency (the first one of each
+    # tunes and captures its handle), then one timed full batch; the GPU is shared by the
+    # frequencies' workers, so the saturated rate is about one batch's
     grid = W.point_sources_plane_grid(n, p, p + 2, 16, 16)
-    cal = [serving.Request(-1, 1, grid[:args.max_cols], 0.0)]
-    tcal = srv.serve(cal, realtime=False)
-    cols_per_s = args.max_cols / tcal * len(omegas)
+    srv.serve([serving.Request(-1 - w, w, grid[:args.max_cols], 0.0) for w in range(len(omegas))], realtime=False)
+    tcal = srv.serve([serving.Request(-9, 1, grid[:args.max_cols], 0.0)], realtime=False)
+    cols_per_s = args.max_cols / tcal
+    log(f"calibration: {tcal:.2f} s per {args.max_cols}-column batch")
     reqs_all = W.serving_requests(n, p, args.requests, 1.0, len(omegas), seed=1801 + 50)
     mean_R = np.mean([min(len(s), args.rmax) for _, _, s in reqs_all])
     rate = 0.8 * cols_per_s / mean_R
@@ -563,10 +572,12 @@ def run_serving(args):
         t += rng.exponential(1.0 / rate)
         reqs.append(serving.Request(i, w, src[:args.rmax], t))
     launches0 = hz.kernel_launches()
-    wall = srv.serve(reqs)
+    wall = srv.serve(reqs, timeout=args.serve_timeout)
     launches = hz.kernel_launches() - launches0
-    st = serving.latency_stats(reqs)
-    total = sum(r.R for r in reqs)
+    done = [r for r in reqs if r.t_done is not None]
+    st = serving.latency_stats(done) if done else None
+    total = sum(r.R for r in done if r.status == 0)
+    log(f"served {len(done)} of {len(reqs)} requests in {wall:.1f} s")
     line = {
         "metric": "serving: online solves/s and p50/p99 request latency (160^3, 3 resident frequencies)",
         "value": total / wall, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
@@ -575,7 +586,8 @@ def run_serving(args):
         "config": {"workload": f"160^3 smooth random, PML 10, 20 layers (local pads {args.npml_local}), "
                                f"3 frequencies, {args.requests} Poisson requests, R ~ U{{1..{args.rmax}}}",
                    "max_cols": args.max_cols, "arrival_rate_per_s": rate},
-        "latency": st, "batches": srv.batches, "max_requests_per_batch": srv.max_requests_per_batch,
+        "latency": st, "requests_done": len(done), "requests_ok": sum(1 for r in done if r.status == 0),
+        "batches": srv.batches, "max_requests_per_batch": srv.max_requests_per_batch,
         "admission": srv.admission_log, "errors": srv.errors, "factor_s": factor_s, "gpu_launches": launches,
         "calibration_s_per_batch": tcal,
     }
@@ -594,6 +606,9 @@ def main():
     ap.add_argument("--rmax", type=int, default=64)
     ap.add_argument("--max-cols", type=int, default=64)
     ap.add_argument("--npml-local", type=int, default=5)
+    ap.add_argument("--serve-timeout", type=float, default=900.0,
+                    help="serving: stop waiting for requests after this many seconds (the line then reports "
+                         "the requests done)")
     ap.add_argument("--config", type=int, default=3, choices=[2, 3, 4, 5],
                     help="3: 128^3 layered+block, R=128 (the headline workload); 2: 64^3 smooth, R=16; "
                          "4: six uneven problems solved as one batch; 5: serving 160^3, 3 frequencies")

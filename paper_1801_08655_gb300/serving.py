@@ -55,7 +55,7 @@ class Server:
     def __init__(self, m: np.ndarray, omegas: Sequence[float], npml: int, C: float, n_layers: int,
                  npml_local: int = -1, precision: str = "mixed", max_cols: int = 64, max_workers: int = 2,
                  opts: Optional[hz.SolveOpts] = None, receivers: Optional[np.ndarray] = None,
-                 mem_reserve_bytes: float = 4e9):
+                 mem_reserve_bytes: float = 4e9, log=None):
         import torch
         self.torch = torch
         self.shape = tuple(m.shape)
@@ -64,6 +64,7 @@ class Server:
         self.opts = opts if opts is not None else hz.default_opts(precision)
         self.receivers = None if receivers is None else np.asarray(receivers, dtype=np.int64)
         self.mem_reserve = float(mem_reserve_bytes)
+        self.log = log          # None or a callable taking one line of progress text
         self.primaries: List[hz.Solver] = []
         for om in omegas:
             s = hz.Solver(m, om, npml, C, n_layers, precision=precision, npml_local=npml_local,
@@ -118,11 +119,16 @@ class Server:
             solver = self.primaries[w]
         self.pending[id(solver)] = need
         self.workers[w].append(solver)
+        if self.log:
+            self.log(f"omega {w}: worker {len(self.workers[w])} admitted")
+        self._start(w, solver)
+        self.admission_log.append(f"omega {w}: worker {len(self.workers[w])} admitted")
+        return True
+
+    def _start(self, w: int, solver: hz.Solver):
         th = threading.Thread(target=self._work, args=(w, solver), daemon=True)
         self.threads.append(th)
         th.start()
-        self.admission_log.append(f"omega {w}: worker {len(self.workers[w])} admitted")
-        return True
 
     # ------------------------------------------------------------------ queue
     def submit(self, req: Request):
@@ -160,7 +166,10 @@ class Server:
                 continue
             try:
                 with torch.cuda.stream(solver.stream):
-                    rhs = torch.zeros((cols, nz, ny, nx), dtype=torch.complex128, device="cuda")
+                    # every batch is solved max_cols wide (unused columns are zero and converge at
+                    # once): one batch signature per handle, so the substitution autotuner and the
+                    # CUDA-graph capture of the matrix-vector product run once, not once per width
+                    rhs = torch.zeros((self.max_cols, nz, ny, nx), dtype=torch.complex128, device="cuda")
                     c = 0
                     for req, a, b in items:
                         src = torch.from_numpy(req.sources[a:b]).to("cuda")
@@ -183,6 +192,9 @@ class Server:
                         c += b - a
                 solver.stream.synchronize()
                 self._deliver(items, outs, time.perf_counter())
+                if self.log:
+                    self.log(f"omega {w}: batch of {cols} columns ({len(items)} items) done, "
+                             f"iterations {info[0].iters}, refinements {info[0].refinements}")
             except Exception as e:  # a failed batch marks its requests; the server keeps going
                 if self._failed_batch(w, solver, items, e):
                     solver.close()
@@ -235,6 +247,8 @@ class Server:
                     self.admission_log.append(f"omega {w}: worker retired after running out of memory")
             if items:
                 self.errors.append(repr(e))
+            if self.log:
+                self.log(f"omega {w}: batch failed ({'out of memory' if oom else repr(e)})")
             for req, a, b in items:
                 req.status = -1
                 req.result = None           # a failed request delivers no partial result
@@ -253,7 +267,11 @@ class Server:
         self.running = True
         with self.cv:
             for w in range(len(self.primaries)):
-                self._admit_worker(w)
+                if self.workers[w]:          # handles admitted by an earlier serve(): run them again
+                    for solver in self.workers[w]:
+                        self._start(w, solver)
+                else:
+                    self._admit_worker(w)
         t0 = time.perf_counter()
         order = sorted(requests, key=lambda r: r.t_arrival)
         offsets = [r.t_arrival for r in order]

@@ -31,6 +31,7 @@ def make_server(free_bytes, need_bytes, monkeypatch):
     srv.threads, srv.errors, srv.admission_log = [], [], []
     srv.pending, srv.retries = {}, {}
     srv.running = True
+    srv.log = None
     srv._work = lambda w, s: None
     monkeypatch.setattr(serving.Server, "worker_bytes", lambda self, cols: need_bytes)
     monkeypatch.setattr(serving.hz.Solver, "shared", classmethod(lambda cls, prim: FakeSolver()))
@@ -93,3 +94,17 @@ def test_failed_item_keeps_request_failed_when_a_later_item_succeeds(monkeypatch
     ok._left = 3
     srv._deliver([(ok, 0, 2), (ok, 2, 3)], [np.full((2, 5), 1.0 + 0j), np.full((1, 5), 2.0 + 0j)], now=2.0)
     assert ok.status == 0 and ok.t_done == 2.0 and ok.result.shape == (3, 5) and ok.result[2, 0] == 2.0
+
+
+def test_a_second_serve_restarts_the_admitted_workers(monkeypatch):
+    """serve() called again (after a calibration run) runs every worker already admitted instead of
+    admitting more: no frequency is left without a running worker."""
+    srv = make_server(free_bytes=100 * GB, need_bytes=1 * GB, monkeypatch=monkeypatch)
+    started = []
+    srv._start = lambda w, solver: started.append((w, solver))
+    srv.running = False
+    srv.serve([], realtime=False, timeout=0.0)
+    assert len(srv.workers[0]) == 1 and started == [(0, srv.primaries[0])]
+    srv.serve([], realtime=False, timeout=0.0)
+    srv.serve([], realtime=False, timeout=0.0)
+    assert len(srv.workers[0]) == 1 and started == [(0, srv.primaries[0])] * 3
