@@ -554,13 +554,17 @@ def run_serving(args):
     srv = serving.Server(m, omegas, p, W.pml_constant(4.5), L, npml_local=args.npml_local, precision="mixed",
                          max_cols=args.max_cols, max_workers=2, opts=opts, receivers=recv, log=log)
     factor_s = time.perf_counter() - t0
-    log(f"factored {len(omegas)} frequencies in {factor_s:.1f} s")
+    log(f"factored {len(omegas)} frequencies in {factor_s:.1f} s; {torch.cuda.mem_get_info()[0] / 1e9:.1f} GB free; "
+        f"worker workspace estimate {srv.worker_bytes(args.max_cols) / 1e9:.1f} GB")
     # calibrate the saturated throughput: full batches at every frequency (the first one of each
     # tunes and captures its handle), then one timed full batch; the GPU is shared by the
     # frequencies' workers, so the saturated rate is about one batch's
     grid = W.point_sources_plane_grid(n, p, p + 2, 16, 16)
     srv.serve([serving.Request(-1 - w, w, grid[:args.max_cols], 0.0) for w in range(len(omegas))], realtime=False)
-    tcal = srv.serve([serving.Request(-9, 1, grid[:args.max_cols], 0.0)], realtime=False)
+    cal = serving.Request(-9, 1, grid[:args.max_cols], 0.0)
+    tcal = srv.serve([cal], realtime=False)
+    if cal.status != 0 or srv.errors:
+        raise SystemExit(f"serving calibration failed: {srv.errors[:2]} (admission: {srv.admission_log[-3:]})")
     cols_per_s = args.max_cols / tcal
     log(f"calibration: {tcal:.2f} s per {args.max_cols}-column batch")
     reqs_all = W.serving_requests(n, p, args.requests, 1.0, len(omegas), seed=1801 + 50)

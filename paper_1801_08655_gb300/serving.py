@@ -227,7 +227,8 @@ class Server:
         failure, or a third out-of-memory failure, marks the requests failed.  Returns whether the
         calling worker must retire (its handle is then closed by the caller)."""
         torch = self.torch
-        oom = (isinstance(e, hz.HzError) and e.status == hz.HZ_ERR_OOM) or \
+        # device memory ran out: an allocation failed, or a solve workspace did not fit (admission)
+        oom = (isinstance(e, hz.HzError) and e.status in (hz.HZ_ERR_OOM, hz.HZ_ERR_ADMISSION)) or \
             isinstance(e, getattr(getattr(torch, "cuda", None), "OutOfMemoryError", ()))
         retire = False
         with self.cv:

@@ -59,6 +59,12 @@ def test_out_of_memory_batch_is_requeued_and_extra_worker_retires(monkeypatch):
     req._left = 40
     items = [(req, 0, 32), (req, 32, 40)]
     oom = hz.HzError(hz.HZ_ERR_OOM, "device allocation failed")
+    adm = hz.HzError(hz.HZ_ERR_ADMISSION, "workspace does not fit")
+    srv._admit_worker(0)
+    extra2 = srv.workers[0][-1]
+    assert srv._failed_batch(0, extra2, items, adm) is True      # a workspace that does not fit: as OOM
+    srv.queues[0].clear()
+    srv.retries.clear()
     assert srv._failed_batch(0, extra, items, oom) is True       # extra worker retires
     assert list(srv.queues[0]) == items                          # same order, at the head
     assert extra not in srv.workers[0] and not srv.errors and req.status == 0
