@@ -134,6 +134,8 @@ void factor_fp64_demote(Ctx& c) {
 
 void release_slots(Ctx& c) {
     c.plans.clear();  // recorded plans point into the slot batches
+    c.setup_plans.clear();
+    c.recon_plans.clear();
     free_batches(c);
     for (void* p : c.slot_acc) cudaFree(p);
     for (void* p : c.slot_x) cudaFree(p);
@@ -193,7 +195,17 @@ void do_solve(Ctx& c, const double2* rhs, int R, double2* u, const hz_solve_opts
     std::vector<hz_solve_info> inf(R);
     for (auto& x : inf) std::memset(&x, 0, sizeof(x));
     const long long N3 = (long long)c.nx * c.ny * c.nz;
-    double* norms = (double*)dev_alloc(2 * R * sizeof(double));
+    // persistent per-handle buffers (grown as needed): per-column norms and, in mixed precision,
+    // the volume residual and correction of the defect-correction passes; reusing them keeps
+    // allocations (and the device-wide synchronisation of cudaFree) out of the solve
+    if (c.norms_cap < R) {
+        if (c.d_norms) cudaFree(c.d_norms);
+        c.d_norms = nullptr;
+        c.norms_cap = 0;
+        c.d_norms = (double*)dev_alloc(2 * (size_t)R * sizeof(double));
+        c.norms_cap = R;
+    }
+    double* norms = c.d_norms;
     std::vector<double> hn(2 * R);
     st_out = HZ_OK;
     try {
@@ -208,9 +220,18 @@ void do_solve(Ctx& c, const double2* rhs, int R, double2* u, const hz_solve_opts
             }
         } else {
             krylov_solve<float2>(c, rhs, true, R, u, o, inf.data());
-            double2* res = (double2*)dev_alloc((size_t)R * N3 * sizeof(double2));
-            double2* du = (double2*)dev_alloc((size_t)R * N3 * sizeof(double2));
-            try {
+            if (c.vol_cap < R) {
+                if (c.d_vol_res) cudaFree(c.d_vol_res);
+                if (c.d_vol_du) cudaFree(c.d_vol_du);
+                c.d_vol_res = c.d_vol_du = nullptr;
+                c.vol_cap = 0;
+                c.d_vol_res = (double2*)dev_alloc((size_t)R * N3 * sizeof(double2));
+                c.d_vol_du = (double2*)dev_alloc((size_t)R * N3 * sizeof(double2));
+                c.vol_cap = R;
+            }
+            double2* res = c.d_vol_res;
+            double2* du = c.d_vol_du;
+            {
                 std::vector<double> g2(R);
                 op_volume_residual(c, rhs, true, u, R, res, norms);
                 d2h(c, hn.data(), norms, 2 * R * sizeof(double));
@@ -241,19 +262,11 @@ void do_solve(Ctx& c, const double2* rhs, int R, double2* u, const hz_solve_opts
                     inf[r].volume_relres = relres(r);
                     if (st_out == HZ_OK && inf[r].volume_relres > o.refine_tol) st_out = HZ_ERR_NO_CONVERGENCE;
                 }
-            } catch (...) {
-                cudaFree(res);
-                cudaFree(du);
-                throw;
             }
-            cudaFree(res);
-            cudaFree(du);
         }
     } catch (...) {
-        cudaFree(norms);
         throw;
     }
-    cudaFree(norms);
     int flags[4];
     d2h(c, flags, c.d_flag, sizeof(flags));
     if (flags[1]) {
@@ -552,6 +565,11 @@ hz_status hz_destroy(hz_handle* h) {
     release_slots(c);
     c.gw.release();
     cudaFree(c.d_flag);
+    if (c.d_io) cudaFree(c.d_io);
+    if (c.h_io) cudaFreeHost(c.h_io);
+    if (c.d_norms) cudaFree(c.d_norms);
+    if (c.d_vol_res) cudaFree(c.d_vol_res);
+    if (c.d_vol_du) cudaFree(c.d_vol_du);
     if (c.owns_shared) {
         for (auto& sh : c.shapes) {
             cudaFree(sh.d_nodes); cudaFree(sh.d_pos); cudaFree(sh.d_upd_idx); cudaFree(sh.d_asm); cudaFree(sh.d_emap);

@@ -175,6 +175,13 @@ struct Ctx {
     bool use_graphs = true;   // replay the GMRES matrix-vector product as a captured CUDA graph
     GmresWork gw;
     std::map<long long, std::unique_ptr<Rec>> plans;   // matvec plans by column count
+    std::map<long long, std::unique_ptr<Rec>> setup_plans, recon_plans;  // by (column count, scaling)
+    void** d_io = nullptr;   // device slots: the current call's volume right-hand side and solution
+    void** h_io = nullptr;   // pinned staging of the two slots
+    double* d_norms = nullptr;           // per-column norm pairs of the volume residual (2 x norms_cap)
+    int norms_cap = 0;
+    double2 *d_vol_res = nullptr, *d_vol_du = nullptr;   // defect correction: residual, correction
+    int vol_cap = 0;                                      // (vol_cap columns of nx*ny*nz each)
     // autotuner: (shape signature, ldc) -> chosen split-K depth and column chunk
     bool autotune = true;
     struct TuneChoice { int KS, CC, tc, KS_tc, min_t, tc_cfg; };

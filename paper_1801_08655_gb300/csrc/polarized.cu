@@ -99,8 +99,10 @@ template <class C> struct VolIO {
 
 // acc[pos(cell)][col0 + r] = S * g[r][z][cell] over the layer's owned planes.
 template <class C>
-__global__ void k_volume_source(const VolIO<C>* io, const double2* g, int R, long long N3, int nx, int ny,
-                                const double2* sx, const double2* sy, const double2* sz, int scale) {
+__global__ void k_volume_source(const VolIO<C>* io, const double2* g, const double2* const* gslot, int R,
+                                long long N3, int nx, int ny, const double2* sx, const double2* sy,
+                                const double2* sz, int scale) {
+    if (gslot) g = *gslot;   // recorded plans read the caller's volume through the handle's slot
     const VolIO<C> q = io[blockIdx.z];
     const int P = nx * ny;
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
@@ -115,7 +117,9 @@ __global__ void k_volume_source(const VolIO<C>* io, const double2* g, int R, lon
 
 // u[r][z][cell] (+)= x[pos(cell)][col0 + r] over the owned planes.
 template <class C>
-__global__ void k_volume_out(const VolIO<C>* io, double2* u, int R, long long N3, int P, int accumulate) {
+__global__ void k_volume_out(const VolIO<C>* io, double2* u, double2* const* uslot, int R, long long N3, int P,
+                             int accumulate) {
+    if (uslot) u = *uslot;
     const VolIO<C> q = io[blockIdx.z];
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
     const int z = q.lo + blockIdx.y;
@@ -555,9 +559,11 @@ std::vector<int> all_layers(const Ctx& ctx) {
     return v;
 }
 
+// g: the volume right-hand side; with gslot != nullptr the kernel reads it from that device slot
+// instead (plans recorded once and replayed for every call)
 template <class C>
 void rec_volume_sources(Ctx& ctx, Rec& rec, const std::vector<int>& layers, const double2* g, bool scale, int R,
-                        int ldc) {
+                        int ldc, const double2* const* gslot = nullptr) {
     std::vector<VolIO<C>> io;
     int maxpl = 0;
     for (int l : layers) {
@@ -576,7 +582,7 @@ void rec_volume_sources(Ctx& ctx, Rec& rec, const std::vector<int>& layers, cons
     const double2 *sx = ctx.d_sx_n, *sy = ctx.d_sy_n, *sz = ctx.d_sz_n;
     const int sc = scale ? 1 : 0;
     rec.add([=](cudaStream_t st) {
-        k_volume_source<C><<<grid, 256, 0, st>>>(d, g, R, N3, nx, ny, sx, sy, sz, sc);
+        k_volume_source<C><<<grid, 256, 0, st>>>(d, g, gslot, R, N3, nx, ny, sx, sy, sz, sc);
         HZ_CHECK_LAUNCH();
     });
 }
@@ -593,13 +599,14 @@ inline void run_now(Ctx& ctx, Rec& rec) {
 // operators (recorders)
 // ------------------------------------------------------------------------------------------
 template <class C>
-void rec_polarized_rhs(Ctx& ctx, Rec& rec, const double2* g, bool scale, int R, double2* fpol) {
+void rec_polarized_rhs(Ctx& ctx, Rec& rec, const double2* g, bool scale, int R, double2* fpol,
+                       const double2* const* gslot = nullptr) {
     const bool dbl = sizeof(C) == 16;
     const int ldc = padded_ldc(dbl, R);
     if (ldc > ctx.slot_cap) throw Error{HZ_ERR_ADMISSION, "too many columns for the layer workspace"};
     auto layers = all_layers(ctx);
     rec_zero_slots<C>(ctx, rec, layers, ldc);
-    rec_volume_sources<C>(ctx, rec, layers, g, scale, R, ldc);
+    rec_volume_sources<C>(ctx, rec, layers, g, scale, R, ldc, gslot);
     rec_subst<C>(ctx, rec, layers, R, false, 2);   // read-outs on the interface planes only
     const size_t bytes = (size_t)R * ctx.ntr * sizeof(double2);
     rec.add([fpol, bytes](cudaStream_t st) { HZ_CUDA(cudaMemsetAsync(fpol, 0, bytes, st)); });
@@ -733,14 +740,14 @@ void rec_apply_precond(Ctx& ctx, Rec& rec, const double2* x, int R, double2* y, 
 // u = reconstruction from f and traces t [R][K][2][P] (Algorithm 2, inner solves).
 template <class C>
 void rec_reconstruct(Ctx& ctx, Rec& rec, const double2* g, bool scale, const double2* t, int R, double2* u,
-                     bool accumulate) {
+                     bool accumulate, const double2* const* gslot = nullptr, double2* const* uslot = nullptr) {
     const bool dbl = sizeof(C) == 16;
     const int L = ctx.L;
     const int ldc = padded_ldc(dbl, R);
     if (ldc > ctx.slot_cap) throw Error{HZ_ERR_ADMISSION, "too many columns for the layer workspace"};
     auto layers = all_layers(ctx);
     rec_zero_slots<C>(ctx, rec, layers, ldc);
-    rec_volume_sources<C>(ctx, rec, layers, g, scale, R, ldc);
+    rec_volume_sources<C>(ctx, rec, layers, g, scale, R, ldc, gslot);
     const long long ts = (long long)ctx.K * 2 * ctx.P;
     std::vector<Inject<C>> inj;
     for (int l = 0; l < L; ++l) {
@@ -765,7 +772,7 @@ void rec_reconstruct(Ctx& ctx, Rec& rec, const double2* g, bool scale, const dou
     const long long N3 = (long long)ctx.nz * ctx.P;
     const int P = (int)ctx.P, acc = accumulate ? 1 : 0;
     rec.add([=](cudaStream_t st) {
-        k_volume_out<C><<<grid, 256, 0, st>>>(d, u, R, N3, P, acc);
+        k_volume_out<C><<<grid, 256, 0, st>>>(d, u, uslot, R, N3, P, acc);
         HZ_CHECK_LAUNCH();
     });
 }
@@ -856,6 +863,8 @@ void ensure_gmres_work(Ctx& ctx, int R, int m) {
     if (g.cap_R >= R && g.m == m) return;
     g.release();
     ctx.plans.clear();
+    ctx.setup_plans.clear();
+    ctx.recon_plans.clear();
     const long long n = ctx.ntr;
     const long long vs = (long long)R * n;
     auto alloc = [&](size_t bytes) {
@@ -901,6 +910,59 @@ Rec& matvec_plan(Ctx& ctx, int R) {
     rec_apply_mpol<C>(ctx, *rec, ctx.gw.in, R, ctx.gw.w2);
     rec_apply_precond<C>(ctx, *rec, ctx.gw.w2, R, ctx.gw.out, ctx.gw.tmp);
     return *ctx.plans.emplace(R, std::move(rec)).first->second;
+}
+
+// Device slots holding the current call's volume pointers (right-hand side, solution), read by the
+// recorded set-up and reconstruction plans; written before each run on the handle's stream.
+inline void set_io(Ctx& ctx, const double2* g, double2* u) {
+    if (!ctx.d_io) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, 2 * sizeof(void*)) != cudaSuccess) {
+            cudaGetLastError();
+            throw Error{HZ_ERR_OOM, "pointer slots"};
+        }
+        ctx.d_io = (void**)p;
+        HZ_CUDA(cudaMallocHost((void**)&ctx.h_io, 2 * sizeof(void*)));
+    }
+    HZ_CUDA(cudaStreamSynchronize(ctx.stream));   // the pinned staging pair is reused by every call
+    ctx.h_io[0] = (void*)g;
+    ctx.h_io[1] = (void*)u;
+    HZ_CUDA(cudaMemcpyAsync(ctx.d_io, ctx.h_io, 2 * sizeof(void*), cudaMemcpyHostToDevice, ctx.stream));
+}
+
+// b = P f_pol for the volume right-hand side in slot 0 (Algorithm 2 up to the trace system), into
+// the Krylov workspace's b; recorded once per (column count, scaling)
+template <class C>
+Rec& setup_plan(Ctx& ctx, int R, bool scale) {
+    const long long key = 2LL * R + (scale ? 1 : 0);
+    auto it = ctx.setup_plans.find(key);
+    if (it != ctx.setup_plans.end()) return *it->second;
+    auto rec = std::make_unique<Rec>();
+    rec->upload_stream = ctx.stream;
+    const double2* const* gslot = (const double2* const*)ctx.d_io;
+    rec_polarized_rhs<C>(ctx, *rec, nullptr, scale, R, ctx.gw.w2, gslot);
+    rec_apply_precond<C>(ctx, *rec, ctx.gw.w2, R, ctx.gw.b, ctx.gw.tmp);
+    return *ctx.setup_plans.emplace(key, std::move(rec)).first->second;
+}
+
+// u (slot 1) from the volume right-hand side (slot 0) and the traces in the workspace's t
+// (Algorithm 2, reconstruction); recorded once per (column count, scaling)
+template <class C>
+Rec& recon_plan(Ctx& ctx, int R, bool scale) {
+    const long long key = 2LL * R + (scale ? 1 : 0);
+    auto it = ctx.recon_plans.find(key);
+    if (it != ctx.recon_plans.end()) return *it->second;
+    auto rec = std::make_unique<Rec>();
+    rec->upload_stream = ctx.stream;
+    rec_reconstruct<C>(ctx, *rec, nullptr, scale, ctx.gw.t, R, nullptr, false,
+                       (const double2* const*)ctx.d_io, (double2* const*)ctx.d_io + 1);
+    return *ctx.recon_plans.emplace(key, std::move(rec)).first->second;
+}
+
+template <class C>
+void run_plan(Ctx& ctx, Rec& rec) {
+    if (ctx.use_graphs && !ctx.prof) rec.run_graph(ctx.stream);
+    else rec.run(ctx.stream);
 }
 
 }  // namespace
@@ -950,13 +1012,8 @@ void gmres_solve(Ctx& ctx, const double2* g, bool scale, int R, double2* u, cons
     std::vector<double> h_resid(R), h_b0(R);
     int total_it = 0;
     // b = P f_pol ; x = 0
-    {
-        Rec rec;
-        rec.upload_stream = st;
-        rec_polarized_rhs<C>(ctx, rec, g, scale, R, W.w2);
-        rec_apply_precond<C>(ctx, rec, W.w2, R, W.b, W.tmp);
-        run_now(ctx, rec);
-    }
+    set_io(ctx, g, u);
+    run_plan<C>(ctx, setup_plan<C>(ctx, R, scale));
     HZ_CUDA(cudaMemsetAsync(W.xs, 0, (size_t)vs * sizeof(double2), st));
     norms(W.b, b0);
     {
@@ -1015,7 +1072,7 @@ void gmres_solve(Ctx& ctx, const double2* g, bool scale, int R, double2* u, cons
     // traces t = x_down + x_up, laid out [R][K][2][P]
     k_lincomb<<<dim3(cdiv(half, TB), R), TB, 0, st>>>(W.t, half, 1.0, W.xs, n, 1.0, W.xs + half, n, half);
     HZ_CHECK_LAUNCH();
-    op_reconstruct<C>(ctx, g, scale, W.t, R, u, false);
+    run_plan<C>(ctx, recon_plan<C>(ctx, R, scale));
     HZ_CUDA(cudaStreamSynchronize(st));
     if (info) {
         for (int r = 0; r < R; ++r) {
@@ -1171,13 +1228,8 @@ void bicgstab_solve(Ctx& ctx, const double2* g, bool scale, int R, double2* u, c
     };
     const double tiny = 1e-300;
     // b = P f_pol; x = 0; r = r^ = b; p = v = 0
-    {
-        Rec rec;
-        rec.upload_stream = st;
-        rec_polarized_rhs<C>(ctx, rec, g, scale, R, W.w2);
-        rec_apply_precond<C>(ctx, rec, W.w2, R, W.b, W.tmp);
-        run_now(ctx, rec);
-    }
+    set_io(ctx, g, u);
+    run_plan<C>(ctx, setup_plan<C>(ctx, R, scale));
     HZ_CUDA(cudaMemsetAsync(W.xs, 0, (size_t)vs * sizeof(double2), st));
     HZ_CUDA(cudaMemsetAsync(p, 0, (size_t)vs * sizeof(double2), st));
     HZ_CUDA(cudaMemsetAsync(v, 0, (size_t)vs * sizeof(double2), st));
@@ -1222,7 +1274,7 @@ void bicgstab_solve(Ctx& ctx, const double2* g, bool scale, int R, double2* u, c
     // traces t = x_down + x_up, laid out [R][K][2][P]
     k_lincomb<<<dim3(cdiv(half, TB), R), TB, 0, st>>>(W.t, half, 1.0, W.xs, n, 1.0, W.xs + half, n, half);
     HZ_CHECK_LAUNCH();
-    op_reconstruct<C>(ctx, g, scale, W.t, R, u, false);
+    run_plan<C>(ctx, recon_plan<C>(ctx, R, scale));
     HZ_CUDA(cudaStreamSynchronize(st));
     if (info) {
         for (int r = 0; r < R; ++r) {
