@@ -11,11 +11,16 @@ int tc_columns(int ldc);   // tensor-core column tile for this leading dimension
 void launch_level_tc(const Batch& b, int h, int mode, int ldc, int* flag, cudaStream_t st);
 int padded_ldc(bool is_double, int ncols);
 
-// Job set with per-level task lists, cached by layer list.  sparse: bit 0 skips the forward
-// products of nodes whose subtree holds none of the layer's interface planes (their right-hand
-// side, and so their forward result, is zero when the sources sit on those planes only); bit 1
-// skips the backward products of such nodes (no read-out below them when only those planes are
-// read).  0 solves everywhere.
+// Sparsity of a batch: which planes of each layer carry the sources (forward code, bits 0-1) and
+// the read-outs (backward code, bits 2-3).  SP_ALL: anywhere (no product skipped); SP_BOTH: the
+// plane pairs next to both internal interfaces; SP_TOP / SP_BOT: the pair next to the top /
+// bottom interface only.  Forward products of nodes whose subtree holds none of the source planes
+// are skipped (their right-hand side, and so their forward result, is zero), and backward
+// products of nodes whose subtree holds none of the read-out planes (nothing below them is read).
+enum { SP_ALL = 0, SP_BOTH = 1, SP_TOP = 2, SP_BOT = 3 };
+constexpr int sparse_code(int fwd, int bwd) { return fwd | (bwd << 2); }
+
+// Job set with per-level task lists, cached by layer list and sparsity code.
 template <class C> Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols, int split = 3, int sparse = 0);
 // Build (or fetch) a batch with an explicit split-K depth and column chunk.
 template <class C> Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS, int CC, bool tc,

@@ -460,12 +460,13 @@ void rec_zero_slots(Ctx& ctx, Rec& rec, const std::vector<int>& layers, int ldc)
 
 // approx: the substitution serves the preconditioner, whose tensor-core products then run with
 // the handle's precond_split TF32 terms
-// sparse: which products may be skipped away from the interface planes (see get_batch); the
-// handle's sparse_subst switch (HZ_SPARSE=0 turns it off) masks it
+// sparse: sparsity code of the batch (sparse_code(fwd, bwd), see get_batch); the handle's
+// sparse_subst switch masks it (HZ_SPARSE: 3 forward and backward, 2 backward only, 0 never)
 template <class C>
 void rec_subst(Ctx& ctx, Rec& rec, const std::vector<int>& layers, int ncols, bool approx = false, int sparse = 0) {
     const int split = approx ? ctx.precond_split : 3;
-    sparse &= ctx.sparse_subst;
+    if (!(ctx.sparse_subst & 1)) sparse &= ~3;          // forward products everywhere
+    if (!(ctx.sparse_subst & 2)) sparse &= ~(3 << 2);   // backward products everywhere
     ensure_tuned<C>(ctx, layers, ncols, split, sparse);  // at record time, before any capture
     const Batch* b = &get_batch<C>(ctx, layers, ncols, split, sparse);
     Ctx* cp = &ctx;
@@ -607,7 +608,7 @@ void rec_polarized_rhs(Ctx& ctx, Rec& rec, const double2* g, bool scale, int R, 
     auto layers = all_layers(ctx);
     rec_zero_slots<C>(ctx, rec, layers, ldc);
     rec_volume_sources<C>(ctx, rec, layers, g, scale, R, ldc, gslot);
-    rec_subst<C>(ctx, rec, layers, R, false, 2);   // read-outs on the interface planes only
+    rec_subst<C>(ctx, rec, layers, R, false, sparse_code(SP_ALL, SP_BOTH));   // read-outs on the interface planes only
     const size_t bytes = (size_t)R * ctx.ntr * sizeof(double2);
     rec.add([fpol, bytes](cudaStream_t st) { HZ_CUDA(cudaMemsetAsync(fpol, 0, bytes, st)); });
     std::vector<Extract<C>> ex;
@@ -655,7 +656,7 @@ void rec_apply_mpol(Ctx& ctx, Rec& rec, const double2* x, int R, double2* y) {
                     inj.push_back(make_inject<C>(ctx, l, false, pair_ptr(x, ctx, dir, l), ntr, ldc, q * R));
             }
         rec_inject<C>(ctx, rec, inj, R);
-        rec_subst<C>(ctx, rec, layers, ncols, false, 3);   // sources and read-outs on the interface planes
+        rec_subst<C>(ctx, rec, layers, ncols, false, sparse_code(SP_BOTH, SP_BOTH));   // sources and read-outs on the interface planes
         std::vector<Extract<C>> ex;
         for (int j = 0; j < K; ++j) {
             // bottom of layer j -> u_down_j: blocks {0 (l>=1), 2 (l>=1), 3}
@@ -693,7 +694,7 @@ void rec_apply_precond(Ctx& ctx, Rec& rec, const double2* x, int R, double2* y, 
         std::vector<int> one{j};
         rec_zero_slots<C>(ctx, rec, one, ldc);
         rec_inject<C>(ctx, rec, {make_inject<C>(ctx, j, true, pair_ptr(y, ctx, 0, j - 1), ntr, ldc, 0)}, R);
-        rec_subst<C>(ctx, rec, one, R, true, 3);
+        rec_subst<C>(ctx, rec, one, R, true, sparse_code(SP_TOP, SP_BOT));   // source on top, read at the bottom
         rec_pairs_axpy(ctx, rec, pair_ptr(y, ctx, 0, j), ntr, pair_ptr(x, ctx, 0, j), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
         std::vector<Extract<C>> ex;
         for (int pl = 0; pl < 2; ++pl)
@@ -715,7 +716,7 @@ void rec_apply_precond(Ctx& ctx, Rec& rec, const double2* x, int R, double2* y, 
             if (l <= L - 2) inj.push_back(make_inject<C>(ctx, l, false, pair_ptr(y, ctx, 0, l), ntr, ldc, 0));
         }
         rec_inject<C>(ctx, rec, inj, R);
-        rec_subst<C>(ctx, rec, layers, R, true, 3);
+        rec_subst<C>(ctx, rec, layers, R, true, sparse_code(SP_BOTH, SP_TOP));   // read at the top only
         std::vector<Extract<C>> ex;
         for (int j = 0; j < K; ++j)
             for (int pl = 0; pl < 2; ++pl)
@@ -728,7 +729,7 @@ void rec_apply_precond(Ctx& ctx, Rec& rec, const double2* x, int R, double2* y, 
         std::vector<int> one{j + 1};
         rec_zero_slots<C>(ctx, rec, one, ldc);
         rec_inject<C>(ctx, rec, {make_inject<C>(ctx, j + 1, false, pair_ptr(y, ctx, 1, j + 1), ntr, ldc, 0)}, R);
-        rec_subst<C>(ctx, rec, one, R, true, 3);
+        rec_subst<C>(ctx, rec, one, R, true, sparse_code(SP_BOT, SP_TOP));   // source at the bottom, read on top
         rec_pairs_axpy(ctx, rec, pair_ptr(y, ctx, 1, j), ntr, pair_ptr(s, ctx, 1, j), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
         std::vector<Extract<C>> ex;
         for (int pl = 0; pl < 2; ++pl)

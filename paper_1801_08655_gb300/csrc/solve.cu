@@ -580,19 +580,30 @@ Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS
     for (int j = 0; j < (int)layers.size(); ++j) {
         const Layer& ly = ctx.layers[layers[j]];
         const Shape& sh = ctx.shapes[ly.shape];
-        // local z planes that carry the interface sources and read-outs of this layer (the plane
-        // pairs next to its internal interfaces); a node whose subtree box misses all of them has
-        // a zero forward result (sparse & 1) / no read-out below it (sparse & 2)
-        std::vector<int> planes;
-        if (layers[j] > 0) { planes.push_back(ly.lo - 1 - ly.zlo); planes.push_back(ly.lo - ly.zlo); }
-        if (layers[j] < ctx.L - 1) { planes.push_back(ly.hi - ly.zlo); planes.push_back(ly.hi + 1 - ly.zlo); }
+        // local z planes that carry the interface sources (forward) and read-outs (backward) of
+        // this layer: the plane pair next to its top interface and/or the pair next to its bottom
+        // interface, as the batch's sparsity code selects (SP_*, forward in bits 0-1, backward in
+        // bits 2-3).  A node whose subtree box misses every forward plane has a zero forward
+        // result; one that misses every backward plane has no read-out below it.
+        auto plane_set = [&](int code) {
+            std::vector<int> pl;
+            const bool top = layers[j] > 0, bot = layers[j] < ctx.L - 1;
+            if (top && (code == SP_BOTH || code == SP_TOP)) { pl.push_back(ly.lo - 1 - ly.zlo); pl.push_back(ly.lo - ly.zlo); }
+            if (bot && (code == SP_BOTH || code == SP_BOT)) { pl.push_back(ly.hi - ly.zlo); pl.push_back(ly.hi + 1 - ly.zlo); }
+            return pl;
+        };
+        const int fcode = sparse & 3, bcode = (sparse >> 2) & 3;
+        const std::vector<int> fplanes = plane_set(fcode), bplanes = plane_set(bcode);
         for (int h = 0; h < (int)sh.levels.size(); ++h)
             for (int nid : sh.levels[h]) {
                 const Node& nd = sh.nodes[nid];
-                bool touches = false;
-                for (int z : planes) touches = touches || (z >= nd.box[4] && z < nd.box[5]);
-                const bool fwd_on = !(sparse & 1) || touches;
-                const bool bwd_on = !(sparse & 2) || touches;
+                auto touches = [&](const std::vector<int>& pl) {
+                    for (int z : pl)
+                        if (z >= nd.box[4] && z < nd.box[5]) return true;
+                    return false;
+                };
+                const bool fwd_on = fcode == SP_ALL || touches(fplanes);
+                const bool bwd_on = bcode == SP_ALL || touches(bplanes);
                 for (int mode = 0; mode < 4; ++mode) {
                     if ((mode == FA || mode == FB) ? !fwd_on : !bwd_on) continue;
                     const int out_t = mode == 1 ? nd.upd_t : nd.own_t;
