@@ -373,6 +373,25 @@ def run_ours(args):
                      "kernels": lines,
                      "substitution_share_of_step": (prof["ms"] / prof_step_ms) if prof_step_ms > 0 else None})
 
+    # flops on the basis of 64-cell nested-dissection leaves: the same solve's products counted over
+    # the factor a 64-cell dissection would store (fewer dense leaf entries); ratio of the
+    # per-column layer-solve flops of the two dissections (symbolic phase only, nothing factored)
+    saved_leaf = os.environ.get("HZ_LEAF")
+    os.environ["HZ_LEAF"] = "64"
+    try:
+        s_leaf = hz.Solver(p.m, p.omega, p.npml, p.C, p.n_layers, precision="mixed", stream=stream, b=bden)
+        f64c = sum(s_leaf.layer_solve_cost(l)[1] for l in range(p.n_layers))
+        s_leaf.close()
+    finally:
+        if saved_leaf is None:
+            os.environ.pop("HZ_LEAF", None)
+        else:
+            os.environ["HZ_LEAF"] = saved_leaf
+    fcur = sum(s.layer_solve_cost(l)[1] for l in range(p.n_layers))
+    roofline["flops_basis"] = "stored factor entries of the 256-cell-leaf dissection"
+    roofline["achieved_64cell_leaf_basis"] = roofline["achieved"] * f64c / fcur if roofline["unit"] == "TFLOP/s" else None
+    roofline["leaf64_to_leaf256_flops_ratio"] = f64c / fcur
+
     # ---------------- error of the headline solve against the stored oracle values
     oracle_err = None
     if R == p.R:

@@ -96,7 +96,7 @@ void hz_default_opts(hz_precision prec, hz_solve_opts* opts);
  * hz_create -- set up a problem (layered decomposition of the Formulation section,
  * Fig. 1 and Eq. 6; symbolic nested dissection of every distinct slab shape).
  *   grid      grid sizes (each >= 3) and spacing h > 0
- *   m         squared slowness, real, nz*ny*nx doubles, host memory; copied
+ *   m         squared slowness, real, nz*ny*nx doubles, host or device (or managed) memory; copied
  *   omega     angular frequency > 0
  *   pml       PML parameters (see hz_pml)
  *   n_layers  number of slabs L, 1 <= L <= number of physical z planes
@@ -132,7 +132,7 @@ hz_status hz_create(const hz_grid* grid, const double* m, double omega, const hz
  * names): the operator is div(b grad u) + omega^2 m u with b = 1/rho, discretized in the same
  * symmetric 7-point form with b at the half nodes (the average of the two nodes; the node itself
  * beyond the grid), so the structure, the method and the boundary are unchanged.
- *   b   1/rho, nz*ny*nx doubles, host memory, every entry finite and > 0; copied.  NULL gives
+ *   b   1/rho, nz*ny*nx doubles, host or device memory, every entry finite and > 0; copied.  NULL gives
  *       b = 1 (exactly hz_create)
  * Other arguments and errors as hz_create, plus HZ_ERR_ARG for b <= 0 and HZ_ERR_NONFINITE for
  * a non-finite b.

@@ -335,6 +335,23 @@ hz_status hz_create_ex(const hz_grid* grid, const double* m, const double* b, do
         const int nphys = nz - 2 * pml->npml;
         if (n_layers < 1 || nphys < n_layers) throw Error{HZ_ERR_ARG, "n_layers out of range"};
         const long long N3 = (long long)grid->nx * grid->ny * grid->nz;
+        // m and b may live in host or device (or managed) memory: device arrays are copied to the
+        // host once here (the checks and the per-layer extensions below read them on the host)
+        std::vector<double> m_copy, b_copy;
+        auto to_host = [&](const double* p, std::vector<double>& buf) -> const double* {
+            cudaPointerAttributes at{};
+            const cudaError_t e = cudaPointerGetAttributes(&at, p);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return p;
+            }
+            if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return p;
+            buf.resize((size_t)N3);
+            HZ_CUDA(cudaMemcpy(buf.data(), p, (size_t)N3 * sizeof(double), cudaMemcpyDefault));
+            return buf.data();
+        };
+        m = to_host(m, m_copy);
+        if (b) b = to_host(b, b_copy);
         for (long long i = 0; i < N3; ++i)
             if (!std::isfinite(m[i])) throw Error{HZ_ERR_NONFINITE, "m has a non-finite entry"};
         if (b)

@@ -573,3 +573,30 @@ def test_bicgstab_config2_against_stored_oracle_samples(hz):
     for r in range(p.R):
         assert rel(uu[r, d["idx"]], d["u"][r]) < E2E_TOL["mixed"], (r, rel(uu[r, d["idx"]], d["u"][r]))
     s.close()
+
+
+def test_create_takes_the_medium_from_device_memory(hz):
+    """hz_create / hz_create_ex accept m (and b) in device memory as well as host memory, with the
+    same factors and solution."""
+    import ctypes as ct
+    p = W.small_problem(16, 3, 2, seed=44, R=2)
+    f = cuda(p.rhs())
+    ref = make_solver(hz, p, "fp64")
+    u_ref = ref.solve(f)[0]
+    ref.close()
+    lib = hz.load()
+    m_dev = torch.from_numpy(np.ascontiguousarray(p.m)).cuda()
+    b_dev = torch.ones_like(m_dev)
+    g = hz.Grid(p.n, p.n, p.n, 1.0)
+    pm = hz.Pml(p.npml, p.C, -1)
+    for use_b in (False, True):
+        hnd = ct.c_void_p()
+        st = lib.hz_create_ex(ct.byref(g), m_dev.data_ptr(), b_dev.data_ptr() if use_b else None, p.omega,
+                              ct.byref(pm), p.n_layers, hz.PREC["fp64"], None, ct.byref(hnd))
+        assert st == hz.HZ_OK, lib.hz_last_error(None)
+        assert lib.hz_factor(hnd) == hz.HZ_OK
+        u = torch.empty_like(f)
+        assert lib.hz_solve(hnd, f.data_ptr(), p.R, u.data_ptr(), None, None) == hz.HZ_OK
+        torch.cuda.synchronize()
+        assert float(torch.linalg.vector_norm(u - u_ref) / torch.linalg.vector_norm(u_ref)) < 1e-12
+        lib.hz_destroy(hnd)
