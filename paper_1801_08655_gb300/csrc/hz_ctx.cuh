@@ -41,6 +41,8 @@ struct Batch {
     int split = 3;                              // TF32 terms per real product on the tensor cores (3 or 1)
     int tc_cfg = 0;                             // tensor-core kernel: 0 one block per work item, 1 persistent
     int sparse = 0;                             // products skipped away from the interface planes (get_batch)
+    int job_cols = 0;                           // columns per job when per-block sparsity splits each
+                                                // layer's columns into jobs (0: one job per layer, ldc wide)
     long long wait_polls = 1LL << 26;           // poll limit of the tensor-core kernels' pipeline waits
     std::vector<long long> pair_off[4], pair_cnt[4];  // tensor-core tasks: two output tiles each
     Task* d_tasks = nullptr;

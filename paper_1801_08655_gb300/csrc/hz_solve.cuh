@@ -20,6 +20,19 @@ int padded_ldc(bool is_double, int ncols);
 enum { SP_ALL = 0, SP_BOTH = 1, SP_TOP = 2, SP_BOT = 3 };
 constexpr int sparse_code(int fwd, int bwd) { return fwd | (bwd << 2); }
 
+// Per-block sparsity: the batch's columns split into nblk (2-4) equal blocks, each with its own
+// sparsity code (block q in bits 4q..4q+3; SP_BLOCKS marks the form, the block count sits in bits
+// 17-19).  Each block is then a job of its own, so that a node product runs only on the column
+// blocks that need it.
+constexpr int SP_BLOCKS = 1 << 16;
+inline int blocked_code(int nblk, const int* codes) {
+    int s = SP_BLOCKS | (nblk << 17);
+    for (int q = 0; q < nblk; ++q) s |= (codes[q] & 15) << (4 * q);
+    return s;
+}
+inline int block_count(int sparse) { return (sparse & SP_BLOCKS) ? (sparse >> 17) & 7 : 1; }
+inline int block_code(int sparse, int q) { return (sparse & SP_BLOCKS) ? (sparse >> (4 * q)) & 15 : sparse; }
+
 // Job set with per-level task lists, cached by layer list and sparsity code.
 template <class C> Batch& get_batch(Ctx& ctx, const std::vector<int>& layers, int ncols, int split = 3, int sparse = 0);
 // Build (or fetch) a batch with an explicit split-K depth and column chunk.

@@ -462,11 +462,33 @@ void rec_zero_slots(Ctx& ctx, Rec& rec, const std::vector<int>& layers, int ldc)
 // the handle's precond_split TF32 terms
 // sparse: sparsity code of the batch (sparse_code(fwd, bwd), see get_batch); the handle's
 // sparse_subst switch masks it (HZ_SPARSE: 3 forward and backward, 2 backward only, 0 never)
+// A per-block code (blocked_code) needs blocks of whole 64-column chunks; otherwise, or when
+// every block has the same code, the batch runs as one job per layer with the union of the codes.
 template <class C>
 void rec_subst(Ctx& ctx, Rec& rec, const std::vector<int>& layers, int ncols, bool approx = false, int sparse = 0) {
     const int split = approx ? ctx.precond_split : 3;
-    if (!(ctx.sparse_subst & 1)) sparse &= ~3;          // forward products everywhere
-    if (!(ctx.sparse_subst & 2)) sparse &= ~(3 << 2);   // backward products everywhere
+    auto mask = [&](int code) {
+        if (!(ctx.sparse_subst & 1)) code &= ~3;          // forward products everywhere
+        if (!(ctx.sparse_subst & 2)) code &= ~(3 << 2);   // backward products everywhere
+        return code;
+    };
+    // plane set covering two: SP_ALL absorbs, two different pairs make SP_BOTH
+    auto join = [](int a, int b) { return (a == SP_ALL || b == SP_ALL) ? SP_ALL : (a == b ? a : SP_BOTH); };
+    const int nblk = block_count(sparse);
+    if (nblk > 1) {
+        int codes[4], fu = -1, bu = -1;
+        bool same = true;
+        for (int q = 0; q < nblk; ++q) {
+            codes[q] = mask(block_code(sparse, q));
+            same = same && codes[q] == codes[0];
+            fu = fu < 0 ? (codes[q] & 3) : join(fu, codes[q] & 3);
+            bu = bu < 0 ? ((codes[q] >> 2) & 3) : join(bu, (codes[q] >> 2) & 3);
+        }
+        const bool whole = ncols % nblk == 0 && (ncols / nblk) % 64 == 0;
+        sparse = (whole && !same) ? blocked_code(nblk, codes) : sparse_code(fu, bu);
+    } else {
+        sparse = mask(sparse);
+    }
     ensure_tuned<C>(ctx, layers, ncols, split, sparse);  // at record time, before any capture
     const Batch* b = &get_batch<C>(ctx, layers, ncols, split, sparse);
     Ctx* cp = &ctx;
@@ -656,7 +678,12 @@ void rec_apply_mpol(Ctx& ctx, Rec& rec, const double2* x, int R, double2* y) {
                     inj.push_back(make_inject<C>(ctx, l, false, pair_ptr(x, ctx, dir, l), ntr, ldc, q * R));
             }
         rec_inject<C>(ctx, rec, inj, R);
-        rec_subst<C>(ctx, rec, layers, ncols, false, sparse_code(SP_BOTH, SP_BOTH));   // sources and read-outs on the interface planes
+        // sources and read-outs on the interface planes, per block: its source pair, and the pairs
+        // read from it (bottom of layer j -> u_down_j, top of layer j+1 -> u_up_j, as extracted below)
+        const int blk_code[4] = {sparse_code(SP_TOP, SP_BOTH), sparse_code(SP_BOT, SP_TOP),
+                                 sparse_code(SP_TOP, SP_BOT), sparse_code(SP_BOT, SP_BOTH)};
+        rec_subst<C>(ctx, rec, layers, ncols, false,
+                     nbk > 1 ? blocked_code(nbk, blk_code + p0) : blk_code[p0]);
         std::vector<Extract<C>> ex;
         for (int j = 0; j < K; ++j) {
             // bottom of layer j -> u_down_j: blocks {0 (l>=1), 2 (l>=1), 3}

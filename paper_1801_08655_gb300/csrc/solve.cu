@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(256, 4) k_subst64(const Task* __restrict__ tas
 
 template <class C, int CC>
 void launch_level(const Batch& b, int h, int mode, int ldc, cudaStream_t st) {
-    const int nchunks = ldc / CC;
+    const int nchunks = (b.job_cols > 0 ? b.job_cols : ldc) / CC;
     const long long off = b.off[mode][h], n = b.cnt[mode][h];
     if (n == 0) return;
     const Task* tasks = b.d_tasks + off;
@@ -562,6 +562,12 @@ Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS
     b.tc_cfg = tc_cfg;
     b.sparse = sparse;
     b.wait_polls = ctx.tc_wait_polls;
+    // per-block sparsity: job j * nblk + q is block q (columns [q * job_cols, (q + 1) * job_cols))
+    // of layer j; the caller has checked that the blocks tile the columns in whole chunks
+    const int nblk = block_count(sparse);
+    if (nblk > 1 && (ncols % nblk != 0 || (ncols / nblk) % 64 != 0 || ldc != ncols))
+        throw Error{HZ_ERR_ARG, "per-block sparsity needs column blocks of a multiple of 64"};
+    b.job_cols = nblk > 1 ? ncols / nblk : 0;
     int H = 0;
     for (int l : layers) H = std::max(H, (int)ctx.shapes[ctx.layers[l].shape].levels.size());
     b.H = H;
@@ -592,8 +598,15 @@ Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS
             if (bot && (code == SP_BOTH || code == SP_BOT)) { pl.push_back(ly.hi - ly.zlo); pl.push_back(ly.hi + 1 - ly.zlo); }
             return pl;
         };
-        const int fcode = sparse & 3, bcode = (sparse >> 2) & 3;
-        const std::vector<int> fplanes = plane_set(fcode), bplanes = plane_set(bcode);
+        int fcode[4], bcode[4];
+        std::vector<int> fplanes[4], bplanes[4];
+        for (int q = 0; q < nblk; ++q) {
+            const int code = block_code(sparse, q);
+            fcode[q] = code & 3;
+            bcode[q] = (code >> 2) & 3;
+            fplanes[q] = plane_set(fcode[q]);
+            bplanes[q] = plane_set(bcode[q]);
+        }
         for (int h = 0; h < (int)sh.levels.size(); ++h)
             for (int nid : sh.levels[h]) {
                 const Node& nd = sh.nodes[nid];
@@ -602,32 +615,40 @@ Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS
                         if (z >= nd.box[4] && z < nd.box[5]) return true;
                     return false;
                 };
-                const bool fwd_on = fcode == SP_ALL || touches(fplanes);
-                const bool bwd_on = bcode == SP_ALL || touches(bplanes);
                 for (int mode = 0; mode < 4; ++mode) {
-                    if ((mode == FA || mode == FB) ? !fwd_on : !bwd_on) continue;
+                    const bool fwd = mode == FA || mode == FB;
                     const int out_t = mode == 1 ? nd.upd_t : nd.own_t;
                     const bool on_tc = tc && tc_node(mode, nd, b.min_t);
-                    // stored factor entries this product reads (triangular L^{-1} or L21)
+                    int nact = 0;
+                    for (int q = 0; q < nblk; ++q) {
+                        const bool on = fwd ? (fcode[q] == SP_ALL || touches(fplanes[q]))
+                                            : (bcode[q] == SP_ALL || touches(bplanes[q]));
+                        if (!on) continue;
+                        ++nact;
+                        const int jq = j * nblk + q;
+                        if (on_tc) {
+                            for (int t = 0; t < out_t; t += 4) {
+                                if (mode == 0) add_tasks(quads[0][h], jq, nid, t, 0, std::min(t + 4, nd.own_t), b.KS_tc);
+                                if (mode == 1) add_tasks(quads[1][h], jq, nid, t, 0, nd.own_t, b.KS_tc);
+                                if (mode == 2) add_tasks(quads[2][h], jq, nid, t, 0, nd.upd_t, b.KS_tc);
+                                if (mode == 3) add_tasks(quads[3][h], jq, nid, t, t, nd.own_t, b.KS_tc);
+                            }
+                        } else {
+                            for (int t = 0; t < out_t; ++t) {
+                                if (mode == 0) add_tasks(lists[0][h], jq, nid, t, 0, t + 1, KS);      // FA: Linv row tile t
+                                if (mode == 1) add_tasks(lists[1][h], jq, nid, t, 0, nd.own_t, KS);   // FB: L21 row tile t
+                                if (mode == 2) add_tasks(lists[2][h], jq, nid, t, 0, nd.upd_t, KS);   // BA (>= 1 task)
+                                if (mode == 3) add_tasks(lists[3][h], jq, nid, t, t, nd.own_t, KS);   // BB
+                            }
+                        }
+                    }
+                    if (nact == 0) continue;
+                    // stored factor entries this product reads (triangular L^{-1} or L21): once
+                    // algorithmically, however many column blocks use them
                     const double ent = (mode == FA || mode == BB) ? (double)nd.nown * (nd.nown + 1) / 2.0
                                                                   : (double)nd.nown * nd.nupd;
                     b.lvl_bytes[on_tc][mode][h] += ent * sizeof(C);
-                    b.lvl_flops[on_tc][mode][h] += 8.0 * ent;
-                    if (on_tc) {
-                        for (int t = 0; t < out_t; t += 4) {
-                            if (mode == 0) add_tasks(quads[0][h], j, nid, t, 0, std::min(t + 4, nd.own_t), b.KS_tc);
-                            if (mode == 1) add_tasks(quads[1][h], j, nid, t, 0, nd.own_t, b.KS_tc);
-                            if (mode == 2) add_tasks(quads[2][h], j, nid, t, 0, nd.upd_t, b.KS_tc);
-                            if (mode == 3) add_tasks(quads[3][h], j, nid, t, t, nd.own_t, b.KS_tc);
-                        }
-                    } else {
-                        for (int t = 0; t < out_t; ++t) {
-                            if (mode == 0) add_tasks(lists[0][h], j, nid, t, 0, t + 1, KS);      // FA: Linv row tile t
-                            if (mode == 1) add_tasks(lists[1][h], j, nid, t, 0, nd.own_t, KS);   // FB: L21 row tile t
-                            if (mode == 2) add_tasks(lists[2][h], j, nid, t, 0, nd.upd_t, KS);   // BA (>= 1 task)
-                            if (mode == 3) add_tasks(lists[3][h], j, nid, t, t, nd.own_t, KS);   // BB
-                        }
-                    }
+                    b.lvl_flops[on_tc][mode][h] += 8.0 * ent * nact / nblk;
                 }
             }
     }
@@ -636,7 +657,7 @@ Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS
     for (int mode = 0; mode < 4; ++mode)
         for (int h = 0; h < H; ++h) {
             auto red_len = [&](const Task& tk) {
-                const Node& nd = ctx.shapes[ctx.layers[layers[tk.job]].shape].nodes[tk.node];
+                const Node& nd = ctx.shapes[ctx.layers[layers[tk.job / nblk]].shape].nodes[tk.node];
                 const int kend = mode == 0 ? std::min(tk.tile + 4, nd.own_t) : (mode == 2 ? nd.upd_t : nd.own_t);
                 return std::min(kend, tk.pad_ + std::min(b.KS_tc, 1 << 28)) - tk.pad_;
             };
@@ -669,14 +690,16 @@ Batch& get_batch_cfg(Ctx& ctx, const std::vector<int>& layers, int ncols, int KS
     for (int l : layers) {
         const Layer& ly = ctx.layers[l];
         const Shape& sh = ctx.shapes[ly.shape];
-        JobDev<C> jd;
-        jd.fac = (const C*)ly.d_fac;
-        jd.dinv = (const C*)ly.d_dinv;
-        jd.nodes = sh.d_nodes;
-        jd.upd_idx = sh.d_upd_idx;
-        jd.acc = (C*)ctx.slot_acc[l];
-        jd.x = (C*)ctx.slot_x[l];
-        jobs.push_back(jd);
+        for (int q = 0; q < nblk; ++q) {
+            JobDev<C> jd;
+            jd.fac = (const C*)ly.d_fac;
+            jd.dinv = (const C*)ly.d_dinv;
+            jd.nodes = sh.d_nodes;
+            jd.upd_idx = sh.d_upd_idx;
+            jd.acc = (C*)ctx.slot_acc[l] + (long long)q * b.job_cols;
+            jd.x = (C*)ctx.slot_x[l] + (long long)q * b.job_cols;
+            jobs.push_back(jd);
+        }
         b.vec_ptrs.push_back({ctx.slot_acc[l], ctx.slot_x[l]});
         b.vec_rows.push_back(sh.N);
     }

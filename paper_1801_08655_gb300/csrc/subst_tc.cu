@@ -639,7 +639,7 @@ int sm_count() {
 template <int NT, int MODE, int SPLIT>
 void launch_one(const Batch& b, const Task* tasks, long long n, const JobDev<float2>* jobs, int ldc, int* flag,
                 cudaStream_t st) {
-    const int nchunks = ldc / NT;
+    const int nchunks = (b.job_cols > 0 ? b.job_cols : ldc) / NT;
     const long long nitems = n * nchunks;
     if (b.tc_cfg == 1) {
         static bool attr = false;
@@ -687,7 +687,7 @@ int tc_columns(int ldc) {
 }
 
 void launch_level_tc(const Batch& b, int h, int mode, int ldc, int* flag, cudaStream_t st) {
-    const bool wide = tc_columns(ldc) == 128;
+    const bool wide = tc_columns(b.job_cols > 0 ? b.job_cols : ldc) == 128;
     if (b.split == 1) {
         if (wide) launch_mode<128, 1>(b, h, mode, ldc, flag, st);
         else launch_mode<64, 1>(b, h, mode, ldc, flag, st);

@@ -457,13 +457,15 @@ def test_tensor_core_factorization_end_to_end(hz, monkeypatch):
     s.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_sparse_substitution_matches_full(hz, precision, monkeypatch):
+@pytest.mark.parametrize("precision,R", [("fp64", 3), ("mixed", 3), ("fp64", 64), ("mixed", 64)])
+def test_sparse_substitution_matches_full(hz, precision, R, monkeypatch):
     """Skipping the products of subtrees away from the interface planes (HZ_SPARSE=3, forward
     and backward) changes neither M_pol, nor the preconditioner, nor the polarized right-hand
     side, nor the end-to-end solution beyond rounding (the skipped products are exactly zero or
-    unread); checked on 6 layers of a smooth medium with thick local pads."""
-    p = W.small_problem(22, 4, 6, seed=43, R=3)
+    unread); checked on 6 layers of a smooth medium with thick local pads.  At R = 64 M_pol's four
+    stacked source blocks are 64-column jobs of their own, each skipping the products its own
+    source and read-out planes do not need."""
+    p = W.small_problem(22, 4, 6, seed=43, R=R)
     rng = np.random.default_rng(11)
     out = {}
     for flag in ("0", "3"):
