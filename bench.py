@@ -282,6 +282,7 @@ def run_ours(args):
     total_ms = 1e3 * replicas.max_over_ranks(sum(step_ms) / 1e3)
     vol_res = max(i.volume_relres for i in step_infos[-1])
     iters = step_infos[-1][0].iters
+    iters_total = step_infos[-1][0].iters_total
     refin = step_infos[-1][0].refinements
 
     # ---------------- end to end through the host-buffer entry point
@@ -472,7 +473,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws}"},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "per": f"batch of {R} right-hand sides"},
-            "gmres_iters": iters, "refinements": refin, "volume_relres_max": vol_res,
+            "gmres_iters": iters, "krylov_iters_all_passes": iters_total, "refinements": refin, "volume_relres_max": vol_res,
             "solve_opts": {"gmres_tol": opts.gmres_tol, "refine_tol": opts.refine_tol,
                            "max_refine": opts.max_refine, "restart": opts.restart,
                            "krylov": "bicgstab" if opts.krylov == 1 else "gmres"},

@@ -69,7 +69,9 @@ typedef struct { int32_t nx, ny, nz; double h; } hz_grid;
 typedef struct { int32_t npml; double C; int32_t npml_local; } hz_pml;
 
 typedef struct {
-    double gmres_tol;    /* stop when ||P(f - M u)|| <= tol ||P f|| per column (default 1e-10 FP64, 1e-7 mixed) */
+    double gmres_tol;    /* stop when ||P(f - M u)|| <= tol ||P f|| per column (default 1e-10 FP64, 1e-7 mixed);
+                            in mixed mode this is the first pass's tolerance: each defect-correction
+                            pass solves to 0.1 refine_tol / (its starting volume residual), capped at 0.1 */
     int32_t restart;     /* Krylov dimension before restart (default 12) */
     int32_t max_iter;    /* total GMRES iterations cap (default 100) */
     double refine_tol;   /* mixed mode: stop refining when ||S f - A u|| <= refine_tol ||S f|| (default 1e-9) */
@@ -85,6 +87,7 @@ typedef struct {
     double trace_relres;   /* final preconditioned relative residual estimate of GMRES */
     double volume_relres;  /* ||S f - A u|| / ||S f|| in FP64 (computed when refining or requested) */
     float ms_total;        /* device time of the whole call for this batch, milliseconds */
+    int32_t iters_total;   /* Krylov iterations of all passes (the first solve and every correction) */
 } hz_solve_info;
 
 typedef struct hz_handle hz_handle;
@@ -183,7 +186,10 @@ hz_status hz_solve_group(hz_handle* const* hs, int32_t n, const double* const* r
 
 /*
  * hz_solve_host -- as hz_solve with HOST rhs and u: copies rhs to the device, solves,
- * copies u back (end-to-end entry point).  Same errors as hz_solve.
+ * copies u back (end-to-end entry point).  Same errors as hz_solve.  The device copies of the two
+ * volumes (2 x R x nx*ny*nz complex128) are kept by the handle for later calls and released by
+ * hz_destroy (or replaced when a later call has more right-hand sides); pinned host buffers
+ * give the fastest copies.
  */
 hz_status hz_solve_host(hz_handle* h, const double* rhs_host, int32_t R, double* u_host,
                         const hz_solve_opts* opts, hz_solve_info* info);

@@ -211,6 +211,7 @@ void do_solve(Ctx& c, const double2* rhs, int R, double2* u, const hz_solve_opts
     try {
         if (c.prec == HZ_PREC_FP64) {
             krylov_solve<double2>(c, rhs, true, R, u, o, inf.data());
+            for (auto& x : inf) x.iters_total = x.iters;
             op_volume_residual(c, rhs, true, u, R, nullptr, norms);
             d2h(c, hn.data(), norms, 2 * R * sizeof(double));
             for (int r = 0; r < R; ++r) {
@@ -220,9 +221,12 @@ void do_solve(Ctx& c, const double2* rhs, int R, double2* u, const hz_solve_opts
             }
         } else {
             krylov_solve<float2>(c, rhs, true, R, u, o, inf.data());
+            for (auto& x : inf) x.iters_total = x.iters;
             if (c.vol_cap < R) {
                 if (c.d_vol_res) cudaFree(c.d_vol_res);
                 if (c.d_vol_du) cudaFree(c.d_vol_du);
+    if (c.d_stage_rhs) cudaFree(c.d_stage_rhs);
+    if (c.d_stage_u) cudaFree(c.d_stage_u);
                 c.d_vol_res = c.d_vol_du = nullptr;
                 c.vol_cap = 0;
                 c.d_vol_res = (double2*)dev_alloc((size_t)R * N3 * sizeof(double2));
@@ -244,16 +248,20 @@ void do_solve(Ctx& c, const double2* rhs, int R, double2* u, const hz_solve_opts
                     if (!std::isfinite(worst)) { st_out = HZ_ERR_NONFINITE; break; }
                     if (worst <= o.refine_tol || passes >= o.max_refine) break;
                     // defect correction: A du = r with the mixed path, u += du.  The correction
-                    // only needs the digits that bring the residual below refine_tol, so its GMRES
-                    // tolerance is relaxed accordingly (never looser than 1e-1).
+                    // needs the digits that bring the residual below refine_tol, with a factor 10
+                    // to spare: its Krylov tolerance is 0.1 refine_tol / (current residual), never
+                    // looser than 1e-1, whatever gmres_tol (which sets the first pass's) is.
                     std::vector<hz_solve_info> inf2(R);
                     hz_solve_opts o2 = o;
-                    o2.gmres_tol = std::max(o.gmres_tol, std::min(1e-1, 0.1 * o.refine_tol / std::max(worst, 1e-300)));
+                    o2.gmres_tol = std::min(1e-1, 0.1 * o.refine_tol / std::max(worst, 1e-300));
                     krylov_solve<float2>(c, res, false, R, du, o2, inf2.data());
                     k_axpy_vol<<<cdiv((long long)R * N3, 256), 256, 0, c.stream>>>(u, du, (long long)R * N3);
                     HZ_CHECK_LAUNCH();
                     ++passes;
-                    for (int r = 0; r < R; ++r) inf[r].iters = inf2[r].iters;
+                    for (int r = 0; r < R; ++r) {
+                        inf[r].iters = inf2[r].iters;
+                        inf[r].iters_total += inf2[r].iters;
+                    }
                     op_volume_residual(c, rhs, true, u, R, res, norms);
                     d2h(c, hn.data(), norms, 2 * R * sizeof(double));
                 }
@@ -552,24 +560,23 @@ hz_status hz_solve_host(hz_handle* h, const double* rhs_host, int32_t R, double*
         Ctx& c = h->ctx;
         if (R < 1 || !rhs_host || !u_host) throw Error{HZ_ERR_ARG, "bad rhs/u/R"};
         const size_t bytes = (size_t)R * c.nx * c.ny * c.nz * sizeof(double2);
-        double* d_rhs = (double*)dev_alloc(bytes);
-        double* d_u = nullptr;
-        hz_status st = HZ_OK;
-        try {
-            d_u = (double*)dev_alloc(bytes);
-            HZ_CUDA(cudaMemcpyAsync(d_rhs, rhs_host, bytes, cudaMemcpyHostToDevice, c.stream));
-            st = hz_solve(h, d_rhs, R, d_u, opts, info);
-            if (st == HZ_OK || st == HZ_ERR_NO_CONVERGENCE) {
-                HZ_CUDA(cudaMemcpyAsync(u_host, d_u, bytes, cudaMemcpyDeviceToHost, c.stream));
-                HZ_CUDA(cudaStreamSynchronize(c.stream));
-            }
-        } catch (...) {
-            cudaFree(d_rhs);
-            if (d_u) cudaFree(d_u);
-            throw;
+        // device copies of the two volumes, kept by the handle (grown as needed) so that a
+        // repeated call neither allocates nor frees (cudaFree synchronises the device)
+        if (c.stage_cap < R) {
+            if (c.d_stage_rhs) cudaFree(c.d_stage_rhs);
+            if (c.d_stage_u) cudaFree(c.d_stage_u);
+            c.d_stage_rhs = c.d_stage_u = nullptr;
+            c.stage_cap = 0;
+            c.d_stage_rhs = (double2*)dev_alloc(bytes);
+            c.d_stage_u = (double2*)dev_alloc(bytes);
+            c.stage_cap = R;
         }
-        cudaFree(d_rhs);
-        cudaFree(d_u);
+        HZ_CUDA(cudaMemcpyAsync(c.d_stage_rhs, rhs_host, bytes, cudaMemcpyHostToDevice, c.stream));
+        const hz_status st = hz_solve(h, (const double*)c.d_stage_rhs, R, (double*)c.d_stage_u, opts, info);
+        if (st == HZ_OK || st == HZ_ERR_NO_CONVERGENCE) {
+            HZ_CUDA(cudaMemcpyAsync(u_host, c.d_stage_u, bytes, cudaMemcpyDeviceToHost, c.stream));
+            HZ_CUDA(cudaStreamSynchronize(c.stream));
+        }
         return st;
     })
 }
@@ -587,6 +594,8 @@ hz_status hz_destroy(hz_handle* h) {
     if (c.d_norms) cudaFree(c.d_norms);
     if (c.d_vol_res) cudaFree(c.d_vol_res);
     if (c.d_vol_du) cudaFree(c.d_vol_du);
+    if (c.d_stage_rhs) cudaFree(c.d_stage_rhs);
+    if (c.d_stage_u) cudaFree(c.d_stage_u);
     if (c.owns_shared) {
         for (auto& sh : c.shapes) {
             cudaFree(sh.d_nodes); cudaFree(sh.d_pos); cudaFree(sh.d_upd_idx); cudaFree(sh.d_asm); cudaFree(sh.d_emap);

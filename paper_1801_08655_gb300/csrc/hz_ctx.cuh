@@ -184,6 +184,8 @@ struct Ctx {
     int norms_cap = 0;
     double2 *d_vol_res = nullptr, *d_vol_du = nullptr;   // defect correction: residual, correction
     int vol_cap = 0;                                      // (vol_cap columns of nx*ny*nz each)
+    double2 *d_stage_rhs = nullptr, *d_stage_u = nullptr; // device copies of hz_solve_host's host
+    int stage_cap = 0;                                    // buffers (stage_cap columns each)
     // autotuner: (shape signature, ldc) -> chosen split-K depth and column chunk
     bool autotune = true;
     struct TuneChoice { int KS, CC, tc, KS_tc, min_t, tc_cfg; };

@@ -47,7 +47,7 @@ class SolveOpts(ct.Structure):
 
 class SolveInfo(ct.Structure):
     _fields_ = [("iters", ct.c_int32), ("refinements", ct.c_int32), ("trace_relres", ct.c_double),
-                ("volume_relres", ct.c_double), ("ms_total", ct.c_float)]
+                ("volume_relres", ct.c_double), ("ms_total", ct.c_float), ("iters_total", ct.c_int32)]
 
 
 class HzError(RuntimeError):

@@ -602,3 +602,24 @@ def test_create_takes_the_medium_from_device_memory(hz):
         torch.cuda.synchronize()
         assert float(torch.linalg.vector_norm(u - u_ref) / torch.linalg.vector_norm(u_ref)) < 1e-12
         lib.hz_destroy(hnd)
+
+
+def test_host_buffer_solve_matches_device_solve(hz):
+    """hz_solve_host (host rhs and u; the handle keeps the device copies between calls) gives the
+    device path's solution, also on a repeated call and on a later call with more right-hand
+    sides (the copies are then replaced), and its solution meets the oracle's."""
+    p = W.small_problem(16, 3, 2, seed=45, R=3)
+    f = p.rhs()
+    s = make_solver(hz, p, "mixed")
+    u_dev = s.solve(cuda(f))[0].cpu().numpy()
+    for R in (2, 2, 3):
+        rhs = np.ascontiguousarray(f[:R])
+        u = np.zeros_like(rhs)
+        out, info, st = s.solve_host(rhs, u=u)
+        assert out is u and st == hz.HZ_OK and len(info) == R
+        # the same refined solution up to the refinement tolerance (float atomics in the
+        # substitution make the rounding order differ from call to call)
+        assert rel(u, u_dev[:R]) < 1e-7, (R, rel(u, u_dev[:R]))
+    s.close()
+    ref = direct.solve(p.m, p.omega, p.npml, p.C, f)
+    assert rel(u_dev, ref) < E2E_TOL["mixed"]
