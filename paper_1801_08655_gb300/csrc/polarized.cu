@@ -168,19 +168,26 @@ __global__ void k_pairs_axpy(double2* y, long long ystride, const double2* x, lo
 // ------------------------------------------------------------------------------------------
 // FP64 volume residual r = g - A u, g = S f (scale) or f, with per-column norms
 // ------------------------------------------------------------------------------------------
-__global__ void k_residual(const double2* f, const double2* u, double2* rout, double* norms, int scale,
-                           int nx, int ny, int nz, const double2* sxn, const double2* isxh,
-                           const double2* syn, const double2* isyh, const double2* szn,
-                           const double2* iszh, const double* m, const double* b, double omega2, double inv_h2) {
+template <int RB>
+__global__ void __launch_bounds__(256) k_residual(const double2* f, const double2* u, double2* rout, double* norms,
+                                                  int scale, int R, int nx, int ny, int nz, const double2* sxn,
+                                                  const double2* isxh, const double2* syn, const double2* isyh,
+                                                  const double2* szn, const double2* iszh, const double* m,
+                                                  const double* b, double omega2, double inv_h2) {
+    // one cell and RB columns per thread: the cell's stencil coefficients (FP64, as in the
+    // assembly) are formed once and applied to RB columns, so that the FP64 pipe (the bound of
+    // this kernel on a GPU whose FP64 rate is a small fraction of its FP32 rate) spends its
+    // work on the products with u
     const long long N3 = (long long)nx * ny * nz;
-    const int r = blockIdx.y;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    double rr = 0.0, gg = 0.0;
+    const int r0 = blockIdx.y * RB;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double rr[RB], gg[RB];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) { rr[j] = 0.0; gg[j] = 0.0; }
     if (i < N3) {
-        int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
-        const double2* ur = u + (long long)r * N3;
-        double2 sx = sxn[x], sy = syn[y], sz = szn[z];
-        double2 syz = cmul(sy, sz), sxz = cmul(sx, sz), sxy = cmul(sx, sy);
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+        const double2 sx = sxn[x], sy = syn[y], sz = szn[z];
+        const double2 syz = cmul(sy, sz), sxz = cmul(sx, sz), sxy = cmul(sx, sy);
         double2 c1 = cscale(cmul(syz, isxh[x]), inv_h2), c2 = cscale(cmul(syz, isxh[x + 1]), inv_h2);
         double2 c3 = cscale(cmul(sxz, isyh[y]), inv_h2), c4 = cscale(cmul(sxz, isyh[y + 1]), inv_h2);
         double2 c5 = cscale(cmul(sxy, iszh[z]), inv_h2), c6 = cscale(cmul(sxy, iszh[z + 1]), inv_h2);
@@ -190,44 +197,59 @@ __global__ void k_residual(const double2* f, const double2* u, double2* rout, do
             c3 = cscale(c3, bhalf(b, i, y, ny, nx, -1)); c4 = cscale(c4, bhalf(b, i, y, ny, nx, +1));
             c5 = cscale(c5, bhalf(b, i, z, nz, pl_, -1)); c6 = cscale(c6, bhalf(b, i, z, nz, pl_, +1));
         }
-        double2 dg = cscale(cmul(sxy, sz), omega2 * m[i]);
+        const double2 sxyz = cmul(sxy, sz);
+        double2 dg = cscale(sxyz, omega2 * m[i]);
         dg = csub(dg, cadd(cadd(cadd(c1, c2), cadd(c3, c4)), cadd(c5, c6)));
-        double2 au = cmul(dg, ur[i]);
-        if (x > 0) au = cadd(au, cmul(c1, ur[i - 1]));
-        if (x < nx - 1) au = cadd(au, cmul(c2, ur[i + 1]));
-        if (y > 0) au = cadd(au, cmul(c3, ur[i - nx]));
-        if (y < ny - 1) au = cadd(au, cmul(c4, ur[i + nx]));
-        long long pl = (long long)nx * ny;
-        if (z > 0) au = cadd(au, cmul(c5, ur[i - pl]));
-        if (z < nz - 1) au = cadd(au, cmul(c6, ur[i + pl]));
-        double2 g = f[(long long)r * N3 + i];
-        if (scale) g = cmul(cmul(sxy, sz), g);
-        double2 res = csub(g, au);
-        if (rout) rout[(long long)r * N3 + i] = res;
-        rr = res.x * res.x + res.y * res.y;
-        gg = g.x * g.x + g.y * g.y;
+        // absent neighbours (outside the box) take a zero coefficient and the cell's own index
+        const long long pl = (long long)nx * ny;
+        const double2 zero = make_double2(0.0, 0.0);
+        const long long ix0 = x > 0 ? i - 1 : i, ix1 = x < nx - 1 ? i + 1 : i;
+        const long long iy0 = y > 0 ? i - nx : i, iy1 = y < ny - 1 ? i + nx : i;
+        const long long iz0 = z > 0 ? i - pl : i, iz1 = z < nz - 1 ? i + pl : i;
+        if (x == 0) c1 = zero;
+        if (x == nx - 1) c2 = zero;
+        if (y == 0) c3 = zero;
+        if (y == ny - 1) c4 = zero;
+        if (z == 0) c5 = zero;
+        if (z == nz - 1) c6 = zero;
+#pragma unroll
+        for (int j = 0; j < RB; ++j) {
+            const int r = r0 + j;
+            if (r >= R) break;
+            const double2* ur = u + (long long)r * N3;
+            double2 au = cmul(dg, ur[i]);
+            au = cadd(au, cmul(c1, ur[ix0]));
+            au = cadd(au, cmul(c2, ur[ix1]));
+            au = cadd(au, cmul(c3, ur[iy0]));
+            au = cadd(au, cmul(c4, ur[iy1]));
+            au = cadd(au, cmul(c5, ur[iz0]));
+            au = cadd(au, cmul(c6, ur[iz1]));
+            double2 g = f[(long long)r * N3 + i];
+            if (scale) g = cmul(sxyz, g);
+            const double2 res = csub(g, au);
+            if (rout) rout[(long long)r * N3 + i] = res;
+            rr[j] = res.x * res.x + res.y * res.y;
+            gg[j] = g.x * g.x + g.y * g.y;
+        }
     }
-    // block reduction
-    for (int o = 16; o > 0; o >>= 1) {
-        rr += __shfl_down_sync(0xffffffffu, rr, o);
-        gg += __shfl_down_sync(0xffffffffu, gg, o);
-    }
-    __shared__ double sr[32], sg[32];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) { sr[w] = rr; sg[w] = gg; }
-    __syncthreads();
-    if (w == 0) {
-        int nw = blockDim.x >> 5;
-        rr = lane < nw ? sr[lane] : 0.0;
-        gg = lane < nw ? sg[lane] : 0.0;
+    // block reductions of the RB column pairs, one atomic pair per column and block
+    __shared__ double sr[RB][8], sg[RB][8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
         for (int o = 16; o > 0; o >>= 1) {
-            rr += __shfl_down_sync(0xffffffffu, rr, o);
-            gg += __shfl_down_sync(0xffffffffu, gg, o);
+            rr[j] += __shfl_down_sync(0xffffffffu, rr[j], o);
+            gg[j] += __shfl_down_sync(0xffffffffu, gg[j], o);
         }
-        if (lane == 0) {
-            atomicAdd(&norms[2 * r], rr);
-            atomicAdd(&norms[2 * r + 1], gg);
-        }
+        if (lane == 0) { sr[j][w] = rr[j]; sg[j][w] = gg[j]; }
+    }
+    __syncthreads();
+    if (threadIdx.x < RB && r0 + (int)threadIdx.x < R) {
+        const int j = threadIdx.x;
+        double a = 0.0, c = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += sr[j][k]; c += sg[j][k]; }
+        atomicAdd(&norms[2 * (r0 + j)], a);
+        atomicAdd(&norms[2 * (r0 + j) + 1], c);
     }
 }
 
@@ -871,10 +893,12 @@ void op_reconstruct(Ctx& ctx, const double2* g, bool scale, const double2* t, in
 void op_volume_residual(Ctx& ctx, const double2* f, bool scale, const double2* u, int R, double2* r, double* norms) {
     long long N3 = (long long)ctx.nx * ctx.ny * ctx.nz;
     HZ_CUDA(cudaMemsetAsync(norms, 0, 2 * R * sizeof(double), ctx.stream));
-    dim3 grid(cdiv(N3, 256), R);
-    k_residual<<<grid, 256, 0, ctx.stream>>>(f, u, r, norms, scale ? 1 : 0, ctx.nx, ctx.ny, ctx.nz, ctx.d_sx_n,
-                                             ctx.d_isx_h, ctx.d_sy_n, ctx.d_isy_h, ctx.d_sz_n, ctx.d_isz_h, ctx.d_m,
-                                             ctx.d_b, ctx.omega * ctx.omega, 1.0 / (ctx.h * ctx.h));
+    constexpr int RB = 8;   // columns per thread
+    dim3 grid(cdiv(N3, 256), cdiv(R, RB));
+    k_residual<RB><<<grid, 256, 0, ctx.stream>>>(f, u, r, norms, scale ? 1 : 0, R, ctx.nx, ctx.ny, ctx.nz,
+                                                 ctx.d_sx_n, ctx.d_isx_h, ctx.d_sy_n, ctx.d_isy_h, ctx.d_sz_n,
+                                                 ctx.d_isz_h, ctx.d_m, ctx.d_b, ctx.omega * ctx.omega,
+                                                 1.0 / (ctx.h * ctx.h));
     HZ_CHECK_LAUNCH();
 }
 
