@@ -29,8 +29,7 @@ namespace {
 
 template <class C> __device__ inline void atomic_addc(C* p, double2 v);
 template <> __device__ inline void atomic_addc<float2>(float2* p, double2 v) {
-    atomicAdd(&p->x, (float)v.x);
-    atomicAdd(&p->y, (float)v.y);
+    atomicAdd(p, make_float2((float)v.x, (float)v.y));
 }
 template <> __device__ inline void atomic_addc<double2>(double2* p, double2 v) {
     atomicAdd(&p->x, v.x);
@@ -48,24 +47,47 @@ template <class C> struct Inject {
     const double* b;         // layer's local b = 1/rho, or nullptr (constant density)
 };
 
+// Trace vectors keep cells contiguous per right-hand side; the slot vectors keep right-hand sides
+// contiguous per row.  The three kernels below move a tile of 32 cells x 32 right-hand sides
+// through shared memory so that both sides are read and written along their contiguous index
+// (tile[a][b] with a pitch of 33 16-byte elements: conflict-free along either index).
+constexpr int IO_T = 32;
+
 template <class C>
-__global__ void k_inject(const Inject<C>* inj, const double2* sx, const double2* sy, double inv_h2,
-                         int nx, int ny) {
+__global__ void __launch_bounds__(256) k_inject(const Inject<C>* inj, const double2* sx, const double2* sy,
+                                                double inv_h2, int nx, int ny, int R) {
+    __shared__ double2 tm[IO_T][IO_T + 1], tp[IO_T][IO_T + 1];   // [r][cell]
     const Inject<C> q = inj[blockIdx.z];
     const int P = nx * ny;
-    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y;
-    if (cell >= P) return;
-    const int x = cell % nx, y = cell / nx;
-    // c = A[(Q,y,x),(P,y,x)]: the z-coupling across the physical half plane between the pair's
-    // planes (zl_m and zl_p are the two of them), times b at that half plane
-    double2 c = cscale(cmul(sx[x], sy[y]), inv_h2);
-    if (q.b) c = cscale(c, 0.5 * (q.b[(long long)q.zl_m * P + cell] + q.b[(long long)q.zl_p * P + cell]));
-    const double2* s = q.src + (long long)r * q.rstride;
-    const double2 vm = cneg(cmul(c, s[q.off_m + cell]));
-    const double2 vp = cmul(c, s[q.off_p + cell]);
-    atomic_addc(q.acc + (long long)q.pos[q.zl_m * P + cell] * q.ldc + q.col0 + r, vm);
-    atomic_addc(q.acc + (long long)q.pos[q.zl_p * P + cell] * q.ldc + q.col0 + r, vp);
+    const int cell0 = blockIdx.x * IO_T, r0 = blockIdx.y * IO_T;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // trace planes, read along cells
+    for (int rr = w; rr < IO_T; rr += 8) {
+        const int r = r0 + rr, cell = cell0 + lane;
+        double2 vm = make_double2(0.0, 0.0), vp = vm;
+        if (r < R && cell < P) {
+            const double2* src = q.src + (long long)r * q.rstride;
+            vm = src[q.off_m + cell];
+            vp = src[q.off_p + cell];
+        }
+        tm[rr][lane] = vm;
+        tp[rr][lane] = vp;
+    }
+    __syncthreads();
+    // slot rows, written along the right-hand sides
+    const int r = r0 + lane;
+    for (int cc = w; cc < IO_T; cc += 8) {
+        const int cell = cell0 + cc;
+        if (cell >= P) break;
+        if (r >= R) continue;
+        const int x = cell % nx, y = cell / nx;
+        // c = A[(Q,y,x),(P,y,x)]: the z-coupling across the physical half plane between the pair's
+        // planes (zl_m and zl_p are the two of them), times b at that half plane
+        double2 c = cscale(cmul(sx[x], sy[y]), inv_h2);
+        if (q.b) c = cscale(c, 0.5 * (q.b[(long long)q.zl_m * P + cell] + q.b[(long long)q.zl_p * P + cell]));
+        atomic_addc(q.acc + (long long)q.pos[q.zl_m * P + cell] * q.ldc + q.col0 + r, cneg(cmul(c, tm[lane][cc])));
+        atomic_addc(q.acc + (long long)q.pos[q.zl_p * P + cell] * q.ldc + q.col0 + r, cmul(c, tp[lane][cc]));
+    }
 }
 
 template <class C> struct Extract {
@@ -79,16 +101,31 @@ template <class C> struct Extract {
 };
 
 template <class C>
-__global__ void k_extract(const Extract<C>* ex, int P) {
+__global__ void __launch_bounds__(256) k_extract(const Extract<C>* ex, int P, int R) {
+    __shared__ double2 t[IO_T][IO_T + 1];   // [cell][r]
     const Extract<C> q = ex[blockIdx.z];
-    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y;
-    if (cell >= P) return;
-    const C* xr = q.x + (long long)q.pos[q.zl * P + cell] * q.ldc + r;
-    double2 s = make_double2(0.0, 0.0);
-    for (int b = 0; b < q.nblk; ++b) s = cadd(s, to_d(xr[q.cols[b]]));
-    double2* d = q.dst + (long long)r * q.rstride + cell;
-    *d = cadd(*d, cscale(s, q.sign));
+    const int cell0 = blockIdx.x * IO_T, r0 = blockIdx.y * IO_T;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // slot rows, read along the right-hand sides (the column blocks summed)
+    for (int cc = w; cc < IO_T; cc += 8) {
+        const int cell = cell0 + cc, r = r0 + lane;
+        double2 v = make_double2(0.0, 0.0);
+        if (cell < P && r < R) {
+            const C* xr = q.x + (long long)q.pos[q.zl * P + cell] * q.ldc + r;
+            for (int b = 0; b < q.nblk; ++b) v = cadd(v, to_d(xr[q.cols[b]]));
+        }
+        t[cc][lane] = v;
+    }
+    __syncthreads();
+    // trace plane, updated along cells
+    const int cell = cell0 + lane;
+    for (int rr = w; rr < IO_T; rr += 8) {
+        const int r = r0 + rr;
+        if (r >= R) break;
+        if (cell >= P) continue;
+        double2* d = q.dst + (long long)r * q.rstride + cell;
+        *d = cadd(*d, cscale(t[lane][rr], q.sign));
+    }
 }
 
 template <class C> struct VolIO {
@@ -97,22 +134,35 @@ template <class C> struct VolIO {
     int ldc, col0, lo, hi, zlo;
 };
 
-// acc[pos(cell)][col0 + r] = S * g[r][z][cell] over the layer's owned planes.
+// acc[pos(cell)][col0 + r] = S * g[r][z][cell] over the layer's owned planes; blockIdx.y is
+// (plane offset) x nrt + (right-hand-side tile).
 template <class C>
-__global__ void k_volume_source(const VolIO<C>* io, const double2* g, const double2* const* gslot, int R,
-                                long long N3, int nx, int ny, const double2* sx, const double2* sy,
-                                const double2* sz, int scale) {
+__global__ void __launch_bounds__(256) k_volume_source(const VolIO<C>* io, const double2* g,
+                                                       const double2* const* gslot, int R, int nrt, long long N3,
+                                                       int nx, int ny, const double2* sx, const double2* sy,
+                                                       const double2* sz, int scale) {
+    __shared__ double2 t[IO_T][IO_T + 1];   // [r][cell]
     if (gslot) g = *gslot;   // recorded plans read the caller's volume through the handle's slot
     const VolIO<C> q = io[blockIdx.z];
     const int P = nx * ny;
-    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    const int z = q.lo + blockIdx.y;
-    if (cell >= P || z > q.hi) return;
-    double2 S = make_double2(1.0, 0.0);
-    if (scale) S = cmul(cmul(sx[cell % nx], sy[cell / nx]), sz[z]);
-    C* dst = q.vec + (long long)q.pos[(z - q.zlo) * P + cell] * q.ldc + q.col0;
-    const double2* src = g + (long long)z * P + cell;
-    for (int r = 0; r < R; ++r) dst[r] = from_d<C>(cmul(S, src[(long long)r * N3]));
+    const int z = q.lo + (int)blockIdx.y / nrt;
+    if (z > q.hi) return;   // uniform over the block
+    const int cell0 = blockIdx.x * IO_T, r0 = ((int)blockIdx.y % nrt) * IO_T;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int rr = w; rr < IO_T; rr += 8) {   // volume, read along cells
+        const int r = r0 + rr, cell = cell0 + lane;
+        t[rr][lane] = (r < R && cell < P) ? g[(long long)r * N3 + (long long)z * P + cell] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    const int r = r0 + lane;
+    for (int cc = w; cc < IO_T; cc += 8) {   // slot rows, written along the right-hand sides
+        const int cell = cell0 + cc;
+        if (cell >= P) break;
+        if (r >= R) continue;
+        double2 S = make_double2(1.0, 0.0);
+        if (scale) S = cmul(cmul(sx[cell % nx], sy[cell / nx]), sz[z]);
+        q.vec[(long long)q.pos[(z - q.zlo) * P + cell] * q.ldc + q.col0 + r] = from_d<C>(cmul(S, t[lane][cc]));
+    }
 }
 
 // u[r][z][cell] (+)= x[pos(cell)][col0 + r] over the owned planes.
@@ -565,12 +615,12 @@ template <class C>
 void rec_inject(Ctx& ctx, Rec& rec, const std::vector<Inject<C>>& v, int R) {
     if (v.empty()) return;
     const Inject<C>* d = rec.up(v);
-    dim3 grid(cdiv(ctx.P, 256), R, (unsigned)v.size());
+    dim3 grid(cdiv(ctx.P, IO_T), cdiv(R, IO_T), (unsigned)v.size());
     const double2 *sx = ctx.d_sx_n, *sy = ctx.d_sy_n;
     const double ih2 = 1.0 / (ctx.h * ctx.h);
     const int nx = ctx.nx, ny = ctx.ny;
     rec.add([=](cudaStream_t st) {
-        k_inject<C><<<grid, 256, 0, st>>>(d, sx, sy, ih2, nx, ny);
+        k_inject<C><<<grid, 256, 0, st>>>(d, sx, sy, ih2, nx, ny, R);
         HZ_CHECK_LAUNCH();
     });
 }
@@ -579,10 +629,10 @@ template <class C>
 void rec_extract(Ctx& ctx, Rec& rec, const std::vector<Extract<C>>& v, int R) {
     if (v.empty()) return;
     const Extract<C>* d = rec.up(v);
-    dim3 grid(cdiv(ctx.P, 256), R, (unsigned)v.size());
+    dim3 grid(cdiv(ctx.P, IO_T), cdiv(R, IO_T), (unsigned)v.size());
     const int P = (int)ctx.P;
     rec.add([=](cudaStream_t st) {
-        k_extract<C><<<grid, 256, 0, st>>>(d, P);
+        k_extract<C><<<grid, 256, 0, st>>>(d, P, R);
         HZ_CHECK_LAUNCH();
     });
 }
@@ -621,13 +671,14 @@ void rec_volume_sources(Ctx& ctx, Rec& rec, const std::vector<int>& layers, cons
         maxpl = std::max(maxpl, ly.hi - ly.lo + 1);
     }
     const VolIO<C>* d = rec.up(io);
-    dim3 grid(cdiv(ctx.P, 256), maxpl, (unsigned)io.size());
+    const int nrt = (int)cdiv(R, IO_T);
+    dim3 grid(cdiv(ctx.P, IO_T), (unsigned)(maxpl * nrt), (unsigned)io.size());
     const long long N3 = (long long)ctx.nz * ctx.P;
     const int nx = ctx.nx, ny = ctx.ny;
     const double2 *sx = ctx.d_sx_n, *sy = ctx.d_sy_n, *sz = ctx.d_sz_n;
     const int sc = scale ? 1 : 0;
     rec.add([=](cudaStream_t st) {
-        k_volume_source<C><<<grid, 256, 0, st>>>(d, g, gslot, R, N3, nx, ny, sx, sy, sz, sc);
+        k_volume_source<C><<<grid, 256, 0, st>>>(d, g, gslot, R, nrt, N3, nx, ny, sx, sy, sz, sc);
         HZ_CHECK_LAUNCH();
     });
 }
