@@ -225,8 +225,6 @@ void do_solve(Ctx& c, const double2* rhs, int R, double2* u, const hz_solve_opts
             if (c.vol_cap < R) {
                 if (c.d_vol_res) cudaFree(c.d_vol_res);
                 if (c.d_vol_du) cudaFree(c.d_vol_du);
-    if (c.d_stage_rhs) cudaFree(c.d_stage_rhs);
-    if (c.d_stage_u) cudaFree(c.d_stage_u);
                 c.d_vol_res = c.d_vol_du = nullptr;
                 c.vol_cap = 0;
                 c.d_vol_res = (double2*)dev_alloc((size_t)R * N3 * sizeof(double2));

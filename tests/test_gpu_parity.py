@@ -607,7 +607,8 @@ def test_create_takes_the_medium_from_device_memory(hz):
 def test_host_buffer_solve_matches_device_solve(hz):
     """hz_solve_host (host rhs and u; the handle keeps the device copies between calls) gives the
     device path's solution, also on a repeated call and on a later call with more right-hand
-    sides (the copies are then replaced), and its solution meets the oracle's."""
+    sides (the copies are then replaced), and its solution meets the oracle's, also when it is the
+    first call of a fresh handle."""
     p = W.small_problem(16, 3, 2, seed=45, R=3)
     f = p.rhs()
     s = make_solver(hz, p, "mixed")
@@ -623,3 +624,11 @@ def test_host_buffer_solve_matches_device_solve(hz):
     s.close()
     ref = direct.solve(p.m, p.omega, p.npml, p.C, f)
     assert rel(u_dev, ref) < E2E_TOL["mixed"]
+    # a host-buffer solve as the first call of a fresh handle: the handle's residual buffers are
+    # created inside that call, after its device copies of rhs and u, and must leave them intact
+    s = make_solver(hz, p, "mixed")
+    u_host, info, st = s.solve_host(f)
+    assert st == hz.HZ_OK and rel(u_host, ref) < E2E_TOL["mixed"], rel(u_host, ref)
+    u_again, _, st = s.solve_host(f)
+    assert st == hz.HZ_OK and rel(u_again, u_host) < 1e-7
+    s.close()
