@@ -31,6 +31,11 @@ in tests/test_oracle_polarized.py against the global direct solve):
 * Algorithm 9 (U) is the mirror image of Algorithm 6: for layer ell, the
   local field due to both of its interfaces' up-going traces, read on its
   bottom pair, minus the input on plane P.
+* Explicit trace-to-trace blocks (trace_blocks): the Local Solves section names them
+  (selective inversion for thin layers) without giving their form; they are read as the local
+  Green's function between the interface pairs, R_rd G^ell R_src^T J_src, with J_src the
+  interface source's weights, which makes E_rs J_s^{-1} = (E_sr J_r^{-1})^T by the complex
+  symmetry of the local operator (pinned).
 * The polarized right-hand side after "algebraic operations and permutations"
   (Polarization subsection, not printed): f_down_j = -(v^j(P_j), v^j(Q_j)),
   f_up_j = -(v^{j+1}(P_j), v^{j+1}(Q_j)), with v^ell the local solution for the
@@ -246,22 +251,100 @@ class PolarizedModel:
         yu = self.sweep_up(ru - self.apply_L(yd))
         return yd, yu
 
+    # ------------------------------------------------------------------ explicit trace blocks
+    def trace_blocks(self):
+        """Explicit trace-to-trace Green's blocks of every layer (the Local Solves section: with
+        selective inversion the local Green's functions restricted to the interfaces can be kept
+        explicitly for thin layers, instead of a pair of triangular solves per application).
+
+        Returns a list over layers of dicts: E[ell][rd + src] with rd, src in {'t', 'b'} is the
+        dense (2P x 2P) matrix taking a trace pair on the layer's top interface (src 't', interface
+        ell-1, through S_top) or bottom interface (src 'b', interface ell, through S_bot) to the
+        layer's top (rd 't': planes P_{ell-1}, Q_{ell-1}) or bottom (rd 'b': P_ell, Q_ell) read-out
+        pair.  Pairs are flattened as (plane, y, x).  Column k is the local solution for the k-th
+        unit trace, so a block is one local solve with 2P right-hand sides."""
+        n, L = self.n, self.L
+        p2 = 2 * n * n
+        unit = np.eye(p2, dtype=np.complex128).reshape(p2, 2, n, n)
+        out = []
+        for ell in range(L):
+            blocks = {}
+            for src in ("t", "b"):
+                if (src == "t" and ell == 0) or (src == "b" and ell == L - 1):
+                    continue
+                inject = self.S_top if src == "t" else self.S_bot
+                G = np.stack([inject(ell, e).ravel() for e in unit], axis=1)
+                W = self.solvers[ell].solve(G).T.reshape(p2, self.nz_local(ell), n, n)
+                if ell >= 1:
+                    blocks["t" + src] = np.stack([self.read_top(ell, w).ravel() for w in W], axis=1)
+                if ell <= L - 2:
+                    blocks["b" + src] = np.stack([self.read_bot(ell, w).ravel() for w in W], axis=1)
+            out.append(blocks)
+        return out
+
+    def _blk(self, B, v):
+        return (B @ v.ravel()).reshape(2, self.n, self.n)
+
+    def apply_Mpol_blocks(self, E, xd, xu):
+        """M_pol from the explicit blocks: the local solves of Algorithms 6-9 replaced by block
+        products.  Down rows: -x_d - [plane P] x_u + E_bt (x_d + x_u) of the interface above +
+        E_bb x_u; up rows: -x_u - [plane Q] x_d + E_tt x_d + E_tb (x_d + x_u) of the interface
+        below (blocks of layer j for down row j, of layer j+1 for up row j)."""
+        K, L = self.K, self.L
+        ud, uu = -xd.copy(), -xu.copy()
+        ud[:, 0] -= xu[:, 0]
+        uu[:, 1] -= xd[:, 1]
+        for j in range(K):
+            if j >= 1:
+                ud[j] += self._blk(E[j]["bt"], xd[j - 1] + xu[j - 1])
+            ud[j] += self._blk(E[j]["bb"], xu[j])
+            uu[j] += self._blk(E[j + 1]["tt"], xd[j])
+            if j + 1 <= L - 2:
+                uu[j] += self._blk(E[j + 1]["tb"], xd[j + 1] + xu[j + 1])
+        return ud, uu
+
+    def apply_P_blocks(self, E, rd, ru):
+        """The preconditioner of Eq. 16 from the explicit blocks: downward sweep (Algorithm 4)
+        y_d_j = E^j_bt y_d_{j-1} - r_d_j; reflections (Algorithm 6) s = r_u - L y_d; upward
+        sweep (Algorithm 5) y_u_j = E^{j+1}_tb y_u_{j+1} - s_j."""
+        K, L = self.K, self.L
+        yd, yu = self.zeros_trace(), self.zeros_trace()
+        yd[0] = -rd[0]
+        for j in range(1, K):
+            yd[j] = self._blk(E[j]["bt"], yd[j - 1]) - rd[j]
+        s = ru.copy()
+        s[:, 1] += yd[:, 1]
+        for j in range(K):
+            s[j] -= self._blk(E[j + 1]["tt"], yd[j])
+            if j + 1 <= L - 2:
+                s[j] -= self._blk(E[j + 1]["tb"], yd[j + 1])
+        yu[K - 1] = -s[K - 1]
+        for j in range(K - 2, -1, -1):
+            yu[j] = self._blk(E[j + 1]["tb"], yu[j + 1]) - s[j]
+        return yd, yu
+
     # ------------------------------------------------------------------ GMRES (Eq. 15)
     def _split(self, v):
         k = self.K * 2 * self.n * self.n
         return v[:k].reshape(self.K, 2, self.n, self.n), v[k:].reshape(self.K, 2, self.n, self.n)
 
-    def solve_traces(self, f, tol=1e-10, restart=40, maxiter=200):
-        """Left-preconditioned GMRES on P M_pol u = P f_pol, x0 = 0; returns (t, iterations)."""
+    def solve_traces(self, f, tol=1e-10, restart=40, maxiter=200, blocks=None):
+        """Left-preconditioned GMRES on P M_pol u = P f_pol, x0 = 0; returns (t, iterations).
+        With `blocks` (from trace_blocks) M_pol and P are applied by explicit block products."""
         if self.L == 1:
             return self.zeros_trace(), 0
+        if blocks is None:
+            Pc, Mp = self.apply_P, self.apply_Mpol
+        else:
+            Pc = lambda a, b: self.apply_P_blocks(blocks, a, b)       # noqa: E731
+            Mp = lambda a, b: self.apply_Mpol_blocks(blocks, a, b)    # noqa: E731
         fd, fu = self.polarized_rhs(f)
-        bd, bu = self.apply_P(fd, fu)
+        bd, bu = Pc(fd, fu)
         b = np.concatenate([bd.ravel(), bu.ravel()])
 
         def mv(v):
             xd, xu = self._split(v)
-            yd, yu = self.apply_P(*self.apply_Mpol(xd, xu))
+            yd, yu = Pc(*Mp(xd, xu))
             return np.concatenate([yd.ravel(), yu.ravel()])
 
         op = spla.LinearOperator((b.size, b.size), matvec=mv, dtype=np.complex128)
@@ -275,9 +358,9 @@ class PolarizedModel:
         xd, xu = self._split(x)
         return xd + xu, its[0]
 
-    def solve(self, f, tol=1e-10):
+    def solve(self, f, tol=1e-10, blocks=None):
         """Full online solve (Algorithm 2) for one right-hand side f (n, n, n)."""
-        t, its = self.solve_traces(f, tol)
+        t, its = self.solve_traces(f, tol, blocks=blocks)
         return self.reconstruct(f, t), its
 
     def traces_of(self, u):
