@@ -243,6 +243,12 @@ def run_ours(args):
     s.factor()
     factor_s = time.perf_counter() - t0
     fstats = s.factor_stats()
+    tblocks = None
+    if args.trace_blocks > 0:
+        # explicit trace-to-trace Green's blocks: M_pol and the preconditioner as block products
+        t0 = time.perf_counter()
+        tb_bytes = s.trace_blocks(args.trace_blocks)
+        tblocks = {"max_cols": args.trace_blocks, "bytes": tb_bytes, "build_s": time.perf_counter() - t0}
     with torch.cuda.stream(stream):
         rhs = torch.zeros((R, n, n, n), dtype=torch.complex128, device=dev)
         for r, (z, y, x) in enumerate(src):
@@ -317,7 +323,7 @@ def run_ours(args):
     prof = s.profile_end()
     stream.synchronize()
     prof_step_ms = ep0.elapsed_time(ep1)
-    kern = [s.profile_kernel(0), s.profile_kernel(1)]
+    kern = [s.profile_kernel(0), s.profile_kernel(1), s.profile_kernel(2)]
     if args.profile_levels:
         print(s.profile_report(), file=sys.stderr, flush=True)
     smx = float(pk.get("sm_max_mhz", 2070.0))
@@ -338,8 +344,9 @@ def run_ours(args):
                 "share_of_step": sec / (prof_step_ms / 1e3) if prof_step_ms > 0 else None}
 
     lines = [kernel_line(kern[0], "k_subst / k_subst64 (CUDA-core substitution)"),
-             kernel_line(kern[1], "k_subst_tcp / k_subst_tc (tcgen05 split-TF32 substitution)")]
-    dom = 1 if kern[1]["ms"] > kern[0]["ms"] else 0
+             kernel_line(kern[1], "k_subst_tcp / k_subst_tc (tcgen05 split-TF32 substitution)"),
+             kernel_line(kern[2], "k_trace_block (explicit trace-to-trace block products)")]
+    dom = max(range(3), key=lambda i: kern[i]["ms"])
     d = lines[dom]
     traffic = measured_traffic(d["kernel"], args.config, R)
     if dom == 1:
@@ -351,7 +358,8 @@ def run_ours(args):
                                   "split issues 3 TF32 MMAs per real product, so the reachable frac is 1/3"),
                     "mma_issue_frac": 3.0 * d["alg_tflops"] / tf32_sus}
     else:
-        # CUDA-core substitution: bound by HBM or by FP32 lanes according to its intensity
+        # CUDA-core substitution or block products: bound by HBM or by FP32 lanes according to
+        # their intensity (8 flops per complex entry and column: R flop/B for complex64 entries)
         inten = d["alg_flops"] / d["alg_bytes"] if d["alg_bytes"] > 0 else 0.0
         hbm_bound = inten < alu_peak * 1e12 / (hbm_peak * 1e9)
         if hbm_bound:
@@ -466,9 +474,14 @@ def run_ours(args):
                                     "mixed precision (complex64 local solves, FP64 GMRES + defect correction)")
                        if args.config == 3 else
                        (f"{W.CONFIG_NAMES[args.config]}{' with smooth random density 1..2.5' if args.density else ''} "
-                        f"(solved with R={R}), mixed precision"),
+                        f"(solved with R={R}), mixed precision"
+                        f"{', M_pol and P by explicit trace-to-trace blocks' if tblocks else ''}"),
                        "n": n, "layers": p.n_layers, "R": R, "precision": "mixed",
-                       "l2": "inputs larger than L2: ~40 GB of factors streamed every GMRES iteration",
+                       "trace_blocks": tblocks,
+                       "l2": ("inputs larger than L2: ~40 GB of factors streamed every GMRES iteration"
+                              if args.config == 3 else
+                              "inputs larger than L2: the layer factors (and explicit trace blocks) streamed "
+                              "every Krylov iteration exceed the 129 MB L2"),
                        "precond_tf32_terms": 1 if os.environ.get("HZ_PRECOND_SPLIT", "3") == "1" else 3,
                        "parallelism": f"replicas x{ws}"},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
@@ -651,6 +664,9 @@ def main():
                     help="GMRES tolerance of the FP64 comparison (1e-5 gives ~1.2e-6 against the oracle)")
     ap.add_argument("--density", action="store_true",
                     help="variable-density workload (64^3 medium with a smooth random density, --config 2)")
+    ap.add_argument("--trace-blocks", type=int, default=0,
+                    help="build the explicit trace-to-trace Green's blocks (hz_trace_blocks) and apply M_pol "
+                         "and the preconditioner by block products for solves of at most this many columns")
     ap.add_argument("--krylov", default="gmres", choices=["gmres", "bicgstab"],
                     help="Krylov solver on the trace system (hz_solve_opts.krylov)")
     args = ap.parse_args()

@@ -254,6 +254,29 @@ hz_status hz_apply_mpol(hz_handle* h, const double* x, int32_t R, double* y);
 /* y = P x, the Gauss-Seidel preconditioner of Eq. 16 (Algorithms 4-6), same layout. */
 hz_status hz_apply_precond(hz_handle* h, const double* x, int32_t R, double* y);
 
+/*
+ * hz_trace_blocks -- explicit trace-to-trace Green's blocks (Local Solves section: with selective
+ * inversion, thin layers can keep the local Green's function between their interface plane pairs
+ * explicitly instead of running a forward and backward substitution per application).  For every
+ * layer it computes the dense 2P x 2P blocks E_rs (P = nx*ny) taking a trace pair on the layer's
+ * top or bottom interface s, through that interface's source, to the layer's top or bottom
+ * read-out pair r: 4L - 6 blocks, one local solve per unit source trace, in the precision of the
+ * handle's local solves (complex64 in the mixed modes, complex128 in FP64).  M_pol and the
+ * preconditioner (hz_apply_mpol, hz_apply_precond and every Krylov iteration of hz_solve) then
+ * apply block products instead of local solves whenever the call has at most max_cols columns;
+ * the right-hand side preparation and the reconstruction keep their local solves.
+ *   max_cols  > 0: build the blocks (once per factorization) and use them up to this many
+ *             columns; 0: release them and return to the local solves everywhere
+ *   bytes     may be NULL; receives the device bytes the blocks hold
+ * The blocks are owned by the handle (released by hz_destroy, by hz_trace_blocks(h, 0, ...), and by
+ * hz_factor, after which they must be built again); handles from hz_create_shared have their own.
+ * Memory: (4L - 6) * 4 P^2 complex elements, 14 GiB at 64^3 with 8 layers in complex64 -- the
+ * blocks pay where layers are thin and right-hand sides few; at 128^3 they do not fit.
+ * Errors: HZ_ERR_ARG (max_cols < 0), HZ_ERR_STATE (not factored), HZ_ERR_OOM / HZ_ERR_ADMISSION
+ * (blocks or the build's workspace do not fit; the handle is left without blocks), HZ_ERR_CUDA.
+ */
+hz_status hz_trace_blocks(hz_handle* h, int32_t max_cols, int64_t* bytes);
+
 /* Reconstruction (Algorithm 2, inner solves): u from f and the traces t = u_down + u_up,
  * t device complex [R][K][2][ny][nx]; u device complex [R][nz][ny][nx]. */
 hz_status hz_reconstruct(hz_handle* h, const double* rhs, const double* t, int32_t R, double* u);
@@ -273,7 +296,9 @@ hz_status hz_volume_residual(hz_handle* h, const double* rhs, const double* u, i
  * of those substitutions; hz_profile_kernel then returns, per kernel kind, the launches, their
  * summed device time in ms and their algorithmic factor bytes and real flops over the interval
  * closed by the last hz_profile_end (kind 0: CUDA-core substitution kernels, 1: tensor-core
- * kernel; any other kind is HZ_ERR_ARG).  Detail mode adds an event pair per launch and
+ * kernel, 2: the explicit trace-block products of hz_trace_blocks, whose bytes are the block
+ * entries each launch reads and whose flops are 8 per entry and column; any other kind is
+ * HZ_ERR_ARG).  Detail mode adds an event pair per launch and
  * replaces CUDA-graph replay by direct launches: profile an interval apart from timed runs.
  * hz_kernel_launches returns the number of kernels the library has launched in this
  * process (all handles).

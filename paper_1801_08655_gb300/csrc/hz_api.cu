@@ -503,6 +503,11 @@ hz_status hz_factor(hz_handle* h) {
     if (!h) return HZ_ERR_ARG;
     HZ_TRY(h, {
         Ctx& c = h->ctx;
+        if (c.tb.base) {   // explicit trace blocks of the previous factors are stale
+            c.tb.release();
+            c.plans.clear();
+            c.setup_plans.clear();
+        }
         const size_t es = elem_size(c);
         for (auto& ly : c.layers) {
             if (!ly.d_fac) {
@@ -586,6 +591,7 @@ hz_status hz_destroy(hz_handle* h) {
     else cudaDeviceSynchronize();
     release_slots(c);
     c.gw.release();
+    c.tb.release();
     cudaFree(c.d_flag);
     if (c.d_io) cudaFree(c.d_io);
     if (c.h_io) cudaFreeHost(c.h_io);
@@ -651,6 +657,34 @@ hz_status hz_create_shared(hz_handle* src, void* stream, hz_handle** out) {
         if (h) { h->ctx.owns_shared = false; hz_destroy(h); }
         return HZ_ERR_OOM;
     }
+}
+
+hz_status hz_trace_blocks(hz_handle* h, int32_t max_cols, int64_t* bytes) {
+    if (bytes) *bytes = 0;
+    if (!h) return HZ_ERR_ARG;
+    HZ_TRY(h, {
+        Ctx& c = h->ctx;
+        if (max_cols < 0) throw Error{HZ_ERR_ARG, "hz_trace_blocks: max_cols must be >= 0"};
+        if (max_cols > 0 && !c.factored) throw Error{HZ_ERR_STATE, "hz_trace_blocks before hz_factor"};
+        HZ_CUDA(cudaStreamSynchronize(c.stream));
+        c.plans.clear();        // recorded M_pol / P applications follow the new setting
+        c.setup_plans.clear();
+        if (max_cols == 0) {
+            c.tb.release();
+            return HZ_OK;
+        }
+        if (c.L >= 2 && !c.tb.base) {
+            const bool dbl = c.prec == HZ_PREC_FP64;
+            const int n2 = (int)(2 * c.P);
+            const int chunk = std::min(256, (n2 + 63) / 64 * 64);
+            ensure_slots(c, padded_ldc(dbl, 2 * chunk), padded_ldc(dbl, 2 * chunk));
+            if (dbl) build_trace_blocks<double2>(c, chunk);
+            else build_trace_blocks<float2>(c, chunk);
+        }
+        c.tb.max_cols = max_cols;
+        if (bytes) *bytes = c.tb.bytes;
+        return HZ_OK;
+    })
 }
 
 const char* hz_last_error(const hz_handle* h) {
@@ -808,8 +842,7 @@ static hz_status profile_begin(hz_handle* h, bool detail) {
         for (auto& r : *v) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
         v->clear();
     }
-    c.kern_stat[0] = KernStat{};
-    c.kern_stat[1] = KernStat{};
+    for (auto& k : c.kern_stat) k = KernStat{};
     c.kern_lvl.clear();
     c.prof = true;
     c.prof_detail = detail;
@@ -866,8 +899,8 @@ hz_status hz_profile_end(hz_handle* h, int64_t* calls, double* total_ms, double*
 hz_status hz_profile_kernel(hz_handle* h, int32_t kind, int64_t* launches, double* total_ms, double* alg_bytes,
                             double* alg_flops) {
     if (!h) return HZ_ERR_ARG;
-    if (kind < 0 || kind > 1) {
-        h->ctx.last_error = "hz_profile_kernel: kind must be 0 (CUDA-core) or 1 (tensor-core)";
+    if (kind < 0 || kind > 2) {
+        h->ctx.last_error = "hz_profile_kernel: kind must be 0 (CUDA-core), 1 (tensor-core) or 2 (trace-block)";
         return HZ_ERR_ARG;
     }
     const KernStat& k = h->ctx.kern_stat[kind];
@@ -917,7 +950,7 @@ const char* hz_factor_report(hz_handle* h) {
 const char* hz_profile_report(hz_handle* h) {
     if (!h) return "";
     Ctx& c = h->ctx;
-    static const char* kinds[2] = {"cuda-core", "tensor-core"};
+    static const char* kinds[3] = {"cuda-core", "tensor-core", "trace-block"};
     static const char* modes[4] = {"FA", "FB", "BA", "BB"};
     c.prof_text = "kind phase level launches tasks ms alg_TFLOP/s\n";
     for (auto& kv : c.kern_lvl) {

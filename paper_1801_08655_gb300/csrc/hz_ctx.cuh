@@ -1,6 +1,7 @@
 // Solver context shared by the translation units (the object behind hz_handle).
 #pragma once
 
+#include <array>
 #include <functional>
 #include <map>
 #include <tuple>
@@ -144,6 +145,26 @@ struct GmresWork {
     }
 };
 
+// Explicit trace-to-trace Green's blocks of the layers (hz_trace_blocks): per layer up to four
+// dense 2P x 2P blocks E_rs, r the read-out pair and s the source pair (0 top, 1 bottom), stored
+// column-major (a unit source trace's 2P read-outs contiguous) in the complex type of the
+// handle's local solves.
+struct TraceBlocks {
+    void* base = nullptr;
+    size_t elem = 0;                             // sizeof the complex type of the blocks
+    long long bytes = 0;
+    std::vector<std::array<long long, 4>> off;   // per layer: element offset of E_rs at [2 r + s], -1 absent
+    int max_cols = 0;                            // M_pol and P use the blocks for at most this many columns
+    void release() {
+        if (base) cudaFree(base);
+        base = nullptr;
+        elem = 0;
+        bytes = 0;
+        off.clear();
+        max_cols = 0;
+    }
+};
+
 struct Ctx {
     // problem
     int nx = 0, ny = 0, nz = 0;
@@ -209,9 +230,11 @@ struct Ctx {
     std::vector<ProfRec> prof_recs;
     bool prof_detail = false;                 // also time every substitution launch by kernel kind
     std::vector<ProfRec> prof_launch;
-    KernStat kern_stat[2];                    // per kind, from the last hz_profile_end
+    KernStat kern_stat[3];                    // per kind (CUDA-core, tensor-core substitution;
+                                              // explicit trace-block products), from the last hz_profile_end
     std::map<std::tuple<int, int, int>, KernStat> kern_lvl;  // per (kind, phase, tree level)
     std::string prof_text;
+    TraceBlocks tb;
 };
 
 template <class C> void factor_layers(Ctx& ctx);

@@ -59,6 +59,11 @@ template <class C> void op_layer_solve(Ctx& ctx, int ell, const double2* g, int 
 void op_volume_residual(Ctx& ctx, const double2* f, bool scale, const double2* u, int R, double2* r,
                         double* norms /* device, 2R: ||r||^2, ||g||^2 */);
 
+// Explicit trace-to-trace Green's blocks of every layer (into ctx.tb), computed by local solves of
+// unit source traces in chunks of at most `chunk` columns per source pair (a multiple of 64; the
+// layer slots must hold 2 * chunk columns).
+template <class C> void build_trace_blocks(Ctx& ctx, int chunk);
+
 struct GmresOut { int iters; double relres; };
 template <class C> void gmres_solve(Ctx& ctx, const double2* g, bool scale, int R, double2* u,
                                     const hz_solve_opts& o, hz_solve_info* info);

@@ -215,6 +215,117 @@ __global__ void k_pairs_axpy(double2* y, long long ystride, const double2* x, lo
     y[(long long)r * ystride + i] = v;
 }
 
+
+// ------------------------------------------------------------------------------------------
+// explicit trace-to-trace Green's blocks (the Local Solves section: selective inversion lets
+// thin layers keep the local Green's function between their interface pairs explicitly)
+// ------------------------------------------------------------------------------------------
+// One term of a block product: E (2P x 2P, column-major, complex type C) applied to the trace
+// pair x0 (+ x1 when given), each pair [r * xstride + k], k < 2P.
+template <class C> struct TBTerm {
+    const C* E;
+    const double2* x0;
+    const double2* x1;
+};
+// y[r * ystride + m] += sign * sum over the terms of (E (x0 + x1))[m], m < 2P, r < R.
+template <class C> struct TBJob {
+    TBTerm<C> t[2];
+    double2* y;
+    int nterm;
+    double sign;
+};
+
+constexpr int TB_ROWS = 256;   // output rows (read-out entries) per block, one per thread
+constexpr int TB_KC = 64;      // source entries staged per step
+
+// Each thread owns one read-out entry m and NC right-hand-side columns; the block streams the
+// columns of E (one unit source trace's read-outs are contiguous, so a warp reads 32 consecutive
+// entries of a column per step) against the source values of TB_KC entries x NC columns staged in
+// shared memory.  blockIdx: x row tile, y (column group, K slice), z job.  With more than one K
+// slice the partial sums are added with FP64 atomics, otherwise each output is read, added to
+// and written by its one thread.
+template <class C, int NC>
+__global__ void __launch_bounds__(TB_ROWS) k_trace_block(const TBJob<C>* jobs, int n2, int R, long long xs,
+                                                         long long ys, int kslice, int ncg) {
+    __shared__ C xsm[TB_KC][NC];
+    const TBJob<C>& jb = jobs[blockIdx.z];
+    const int m = blockIdx.x * TB_ROWS + threadIdx.x;
+    const int cg = blockIdx.y % ncg, ks = blockIdx.y / ncg;
+    const int c0 = cg * NC;
+    const int kb = ks * kslice, ke = min(n2, kb + kslice);
+    C acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = czero<C>();
+    const int nterm = jb.nterm;
+    for (int t = 0; t < nterm; ++t) {
+        const C* E = jb.t[t].E;
+        const double2* x0 = jb.t[t].x0;
+        const double2* x1 = jb.t[t].x1;
+        for (int kc = kb; kc < ke; kc += TB_KC) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < TB_KC * NC; i += TB_ROWS) {
+                const int kk = i % TB_KC, c = i / TB_KC;
+                const int k = kc + kk, r = c0 + c;
+                double2 v = make_double2(0.0, 0.0);
+                if (k < ke && r < R) {
+                    v = x0[(long long)r * xs + k];
+                    if (x1) v = cadd(v, x1[(long long)r * xs + k]);
+                }
+                xsm[kk][c] = from_d<C>(v);
+            }
+            __syncthreads();
+            const int kn = min(TB_KC, ke - kc);
+            if (m < n2) {
+                const C* Ep = E + (long long)kc * n2 + m;
+                for (int kk = 0; kk < kn; kk += 8) {
+                    C e[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) e[u] = (kk + u < kn) ? __ldcs(Ep + (long long)(kk + u) * n2) : czero<C>();
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) cfma(acc[c], e[u], xsm[kk + u][c]);
+                }
+            }
+        }
+    }
+    if (m >= n2) return;
+    const bool atomic = gridDim.y > (unsigned)ncg;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int r = c0 + c;
+        if (r >= R) break;
+        const double2 v = cscale(to_d(acc[c]), jb.sign);
+        double2* yp = jb.y + (long long)r * ys + m;
+        if (atomic) {
+            atomicAdd(&yp->x, v.x);
+            atomicAdd(&yp->y, v.y);
+        } else {
+            *yp = cadd(*yp, v);
+        }
+    }
+}
+
+// U[r][k] = (k == k0 + r), r < ncols, k < n2: unit source traces k0 .. k0 + ncols - 1 (pairs
+// flattened as (plane, cell)); columns past the last trace stay zero.
+__global__ void k_unit_traces(double2* U, int n2, int ncols, int k0) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)ncols * n2) return;
+    const int r = (int)(i / n2), k = (int)(i % n2);
+    U[i] = make_double2(k == k0 + r ? 1.0 : 0.0, 0.0);
+}
+
+// E_b[(k0 + r) * n2 + m] = T[b][r][m] for the chunk's columns r < ncols with k0 + r < n2.
+template <class C>
+__global__ void k_store_blocks(C* base, const long long* off, const double2* T, int n2, int ncols, int k0) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (i >= (long long)ncols * n2) return;
+    const int r = (int)(i / n2), m = (int)(i % n2);
+    if (k0 + r >= n2) return;
+    base[off[b] + (long long)(k0 + r) * n2 + m] = from_d<C>(T[(long long)b * ncols * n2 + i]);
+}
+
 // ------------------------------------------------------------------------------------------
 // FP64 volume residual r = g - A u, g = S f (scale) or f, with per-column norms
 // ------------------------------------------------------------------------------------------
@@ -689,7 +800,247 @@ inline void run_now(Ctx& ctx, Rec& rec) {
     HZ_CUDA(cudaStreamSynchronize(ctx.stream));
 }
 
+// ------------------------------------------------------------------------------------------
+// operators on the explicit trace-to-trace blocks
+// ------------------------------------------------------------------------------------------
+template <class C>
+bool use_trace_blocks(const Ctx& ctx, int R) {
+    return ctx.tb.base && ctx.tb.elem == sizeof(C) && R <= ctx.tb.max_cols;
+}
+
+// E_rs of layer l (r, s: 0 top, 1 bottom); the caller only asks for blocks that exist
+template <class C>
+const C* trace_block(const Ctx& ctx, int l, int r, int s) {
+    const long long o = ctx.tb.off[l][2 * r + s];
+    if (o < 0) throw Error{HZ_ERR_STATE, "explicit trace block missing"};
+    return (const C*)ctx.tb.base + o;
+}
+
+template <class C, int NC>
+void launch_trace_block(const TBJob<C>* d, unsigned njobs, int n2, int R, long long xs, long long ys, int ksplit,
+                        int kslice, int ncg, cudaStream_t st) {
+    dim3 grid(cdiv(n2, TB_ROWS), (unsigned)(ncg * ksplit), njobs);
+    k_trace_block<C, NC><<<grid, TB_ROWS, 0, st>>>(d, n2, R, xs, ys, kslice, ncg);
+    HZ_CHECK_LAUNCH();
+}
+
+// One launch of block products over independent jobs (distinct outputs), on trace pairs of
+// vectors with the trace-vector stride.  Outputs must hold their other terms already.  Enough
+// K slices are used to give the GPU about two blocks per SM.
+template <class C>
+void rec_trace_blocks(Ctx& ctx, Rec& rec, const std::vector<TBJob<C>>& jobs, int R) {
+    if (jobs.empty()) return;
+    const bool dbl = sizeof(C) == 16;
+    const int n2 = (int)(2 * ctx.P);
+    const int NC = (R <= 8) ? 8 : (dbl || R <= 16) ? 16 : 32;
+    const int ncg = cdiv(R, NC);
+    int sms = 0;
+    HZ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx.device));
+    const long long base = (long long)cdiv(n2, TB_ROWS) * ncg * (long long)jobs.size();
+    int ksplit = (int)std::max<long long>(1, std::min<long long>((2LL * sms) / std::max<long long>(1, base),
+                                                                 std::max(1, n2 / (4 * TB_KC))));
+    const int kslice = cdiv(cdiv(n2, ksplit), TB_KC) * TB_KC;
+    ksplit = cdiv(n2, kslice);
+    const TBJob<C>* d = rec.up(jobs);
+    const unsigned nj = (unsigned)jobs.size();
+    const long long xs = ctx.ntr, ys = ctx.ntr;
+    // algorithmic work of the launch: every block entry read once; 8 real flops per entry and column
+    long long terms = 0;
+    for (const auto& j : jobs) terms += j.nterm;
+    const double lbytes = (double)terms * n2 * (double)n2 * sizeof(C);
+    const double lflops = 8.0 * terms * n2 * (double)n2 * R;
+    Ctx* cp = &ctx;
+    rec.add([=](cudaStream_t st) {
+        ProfRec pr{};
+        const bool timed = cp->prof && cp->prof_detail;   // never during a graph capture (prof off)
+        if (timed) {
+            HZ_CUDA(cudaEventCreate(&pr.e0));
+            HZ_CUDA(cudaEventCreate(&pr.e1));
+            HZ_CUDA(cudaEventRecord(pr.e0, st));
+        }
+        if (NC == 8) launch_trace_block<C, 8>(d, nj, n2, R, xs, ys, ksplit, kslice, ncg, st);
+        else if (NC == 16) launch_trace_block<C, 16>(d, nj, n2, R, xs, ys, ksplit, kslice, ncg, st);
+        else launch_trace_block<C, (sizeof(C) == 16 ? 16 : 32)>(d, nj, n2, R, xs, ys, ksplit, kslice, ncg, st);
+        if (timed) {
+            HZ_CUDA(cudaEventRecord(pr.e1, st));
+            pr.kind = 2;
+            pr.mode = 0;
+            pr.level = 0;
+            pr.tasks = nj;
+            pr.bytes = lbytes;
+            pr.flops = lflops;
+            cp->prof_launch.push_back(pr);
+        }
+    });
+}
+
+template <class C>
+TBJob<C> tb_job(double2* y, double sign) {
+    TBJob<C> j;
+    j.t[0] = j.t[1] = TBTerm<C>{nullptr, nullptr, nullptr};
+    j.y = y;
+    j.nterm = 0;
+    j.sign = sign;
+    return j;
+}
+template <class C>
+void tb_term(TBJob<C>& j, const C* E, const double2* x0, const double2* x1 = nullptr) {
+    j.t[j.nterm++] = TBTerm<C>{E, x0, x1};
+}
+
+// y = M_pol x with the local solves replaced by block products: down row j gets
+// E^j_bt (x_down + x_up)_{j-1} + E^j_bb x_up_j, up row j gets E^{j+1}_tt x_down_j +
+// E^{j+1}_tb (x_down + x_up)_{j+1} (the read-outs the stacked solve of rec_apply_mpol sums).
+template <class C>
+void rec_apply_mpol_blocks(Ctx& ctx, Rec& rec, const double2* x, int R, double2* y) {
+    const int K = ctx.K, L = ctx.L;
+    const long long ntr = ctx.ntr;
+    rec_pairs_axpy(ctx, rec, pair_ptr(y, ctx, 0, 0), ntr, pair_ptr(x, ctx, 0, 0), ntr, -1.0, pair_ptr(x, ctx, 1, 0), ntr,
+                   -1.0, 0, K, R);
+    rec_pairs_axpy(ctx, rec, pair_ptr(y, ctx, 1, 0), ntr, pair_ptr(x, ctx, 1, 0), ntr, -1.0, pair_ptr(x, ctx, 0, 0), ntr,
+                   -1.0, 1, K, R);
+    std::vector<TBJob<C>> jobs;
+    for (int j = 0; j < K; ++j) {
+        TBJob<C> dn = tb_job<C>(pair_ptr(y, ctx, 0, j), 1.0);
+        if (j >= 1) tb_term(dn, trace_block<C>(ctx, j, 1, 0), pair_ptr(x, ctx, 0, j - 1), pair_ptr(x, ctx, 1, j - 1));
+        tb_term(dn, trace_block<C>(ctx, j, 1, 1), pair_ptr(x, ctx, 1, j));
+        jobs.push_back(dn);
+        TBJob<C> up = tb_job<C>(pair_ptr(y, ctx, 1, j), 1.0);
+        tb_term(up, trace_block<C>(ctx, j + 1, 0, 0), pair_ptr(x, ctx, 0, j));
+        if (j + 1 <= L - 2)
+            tb_term(up, trace_block<C>(ctx, j + 1, 0, 1), pair_ptr(x, ctx, 0, j + 1), pair_ptr(x, ctx, 1, j + 1));
+        jobs.push_back(up);
+    }
+    rec_trace_blocks<C>(ctx, rec, jobs, R);
+}
+
+// y = P x (Eq. 16) on the blocks: down sweep y_down_j = E^j_bt y_down_{j-1} - x_down_j; reflections
+// s_j = x_up_j + [Q] y_down_j - E^{j+1}_tt y_down_j - E^{j+1}_tb y_down_{j+1}; up sweep
+// y_up_j = E^{j+1}_tb y_up_{j+1} - s_j.  tmp: one trace vector of scratch (s in its up half).
+template <class C>
+void rec_apply_precond_blocks(Ctx& ctx, Rec& rec, const double2* x, int R, double2* y, double2* tmp) {
+    const int K = ctx.K, L = ctx.L;
+    const long long ntr = ctx.ntr;
+    rec_pairs_axpy(ctx, rec, pair_ptr(y, ctx, 0, 0), ntr, pair_ptr(x, ctx, 0, 0), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
+    for (int j = 1; j < K; ++j) {
+        rec_pairs_axpy(ctx, rec, pair_ptr(y, ctx, 0, j), ntr, pair_ptr(x, ctx, 0, j), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
+        TBJob<C> jb = tb_job<C>(pair_ptr(y, ctx, 0, j), 1.0);
+        tb_term(jb, trace_block<C>(ctx, j, 1, 0), pair_ptr(y, ctx, 0, j - 1));
+        rec_trace_blocks<C>(ctx, rec, {jb}, R);
+    }
+    double2* s = tmp;
+    rec_pairs_axpy(ctx, rec, pair_ptr(s, ctx, 1, 0), ntr, pair_ptr(x, ctx, 1, 0), ntr, 1.0, pair_ptr(y, ctx, 0, 0), ntr,
+                   1.0, 1, K, R);
+    {
+        std::vector<TBJob<C>> jobs;
+        for (int j = 0; j < K; ++j) {
+            TBJob<C> jb = tb_job<C>(pair_ptr(s, ctx, 1, j), -1.0);
+            tb_term(jb, trace_block<C>(ctx, j + 1, 0, 0), pair_ptr(y, ctx, 0, j));
+            if (j + 1 <= L - 2) tb_term(jb, trace_block<C>(ctx, j + 1, 0, 1), pair_ptr(y, ctx, 0, j + 1));
+            jobs.push_back(jb);
+        }
+        rec_trace_blocks<C>(ctx, rec, jobs, R);
+    }
+    rec_pairs_axpy(ctx, rec, pair_ptr(y, ctx, 1, K - 1), ntr, pair_ptr(s, ctx, 1, K - 1), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
+    for (int j = K - 2; j >= 0; --j) {
+        rec_pairs_axpy(ctx, rec, pair_ptr(y, ctx, 1, j), ntr, pair_ptr(s, ctx, 1, j), ntr, -1.0, nullptr, 0, 0.0, 0, 1, R);
+        TBJob<C> jb = tb_job<C>(pair_ptr(y, ctx, 1, j), 1.0);
+        tb_term(jb, trace_block<C>(ctx, j + 1, 0, 1), pair_ptr(y, ctx, 1, j + 1));
+        rec_trace_blocks<C>(ctx, rec, {jb}, R);
+    }
+}
+
 }  // namespace
+
+// Explicit blocks of every layer: unit source traces, `chunk` at a time, injected through S_top
+// (column block 0) and S_bot (column block 1) of every layer at once, solved, and read at the
+// layer's top and bottom pairs; the read-outs of the chunk become columns k0 .. k0 + chunk - 1 of
+// the blocks.
+template <class C>
+void build_trace_blocks(Ctx& ctx, int chunk) {
+    const bool dbl = sizeof(C) == 16;
+    const int L = ctx.L;
+    const int n2 = (int)(2 * ctx.P);
+    if (chunk < 64 || chunk % 64 || padded_ldc(dbl, 2 * chunk) > ctx.slot_cap)
+        throw Error{HZ_ERR_ARG, "trace block chunk does not fit the layer workspace"};
+    const int ldc = padded_ldc(dbl, 2 * chunk);
+    TraceBlocks tb;
+    tb.elem = sizeof(C);
+    tb.off.assign(L, {-1, -1, -1, -1});
+    struct Blk { int l, r, s; };
+    std::vector<Blk> blks;
+    long long nb = 0;
+    for (int l = 0; l < L; ++l)
+        for (int r = 0; r < 2; ++r)
+            for (int s = 0; s < 2; ++s) {
+                if ((r == 0 || s == 0) && l == 0) continue;       // no top interface
+                if ((r == 1 || s == 1) && l == L - 1) continue;   // no bottom interface
+                tb.off[l][2 * r + s] = nb * (long long)n2 * n2;
+                blks.push_back({l, r, s});
+                ++nb;
+            }
+    tb.bytes = nb * (long long)n2 * n2 * (long long)sizeof(C);
+    if (cudaMalloc(&tb.base, std::max<long long>(tb.bytes, 16)) != cudaSuccess) {
+        cudaGetLastError();
+        tb.base = nullptr;
+        throw Error{HZ_ERR_OOM, "explicit trace blocks (" + std::to_string(tb.bytes >> 20) + " MiB) do not fit"};
+    }
+    double2 *U = nullptr, *T = nullptr;
+    long long* d_off = nullptr;
+    auto cleanup = [&]() {
+        if (U) cudaFree(U);
+        if (T) cudaFree(T);
+        if (d_off) cudaFree(d_off);
+    };
+    try {
+        const size_t ubytes = (size_t)chunk * n2 * sizeof(double2);
+        const size_t tbytes = (size_t)nb * chunk * n2 * sizeof(double2);
+        if (cudaMalloc((void**)&U, ubytes) != cudaSuccess || cudaMalloc((void**)&T, tbytes) != cudaSuccess ||
+            cudaMalloc((void**)&d_off, nb * sizeof(long long)) != cudaSuccess) {
+            cudaGetLastError();
+            throw Error{HZ_ERR_OOM, "trace block staging does not fit"};
+        }
+        std::vector<long long> h_off;
+        for (const Blk& b : blks) h_off.push_back(tb.off[b.l][2 * b.r + b.s]);
+        HZ_CUDA(cudaMemcpyAsync(d_off, h_off.data(), nb * sizeof(long long), cudaMemcpyHostToDevice, ctx.stream));
+        Rec rec;
+        rec.upload_stream = ctx.stream;
+        auto layers = all_layers(ctx);
+        rec_zero_slots<C>(ctx, rec, layers, ldc);
+        std::vector<Inject<C>> inj;
+        for (int l = 0; l < L; ++l) {
+            if (l >= 1) inj.push_back(make_inject<C>(ctx, l, true, U, n2, ldc, 0));
+            if (l <= L - 2) inj.push_back(make_inject<C>(ctx, l, false, U, n2, ldc, chunk));
+        }
+        rec_inject<C>(ctx, rec, inj, chunk);
+        const int codes[2] = {sparse_code(SP_TOP, SP_BOTH), sparse_code(SP_BOT, SP_BOTH)};
+        rec_subst<C>(ctx, rec, layers, 2 * chunk, false, blocked_code(2, codes));
+        rec.add([T, tbytes](cudaStream_t st) { HZ_CUDA(cudaMemsetAsync(T, 0, tbytes, st)); });
+        std::vector<Extract<C>> ex;
+        for (long long b = 0; b < nb; ++b)
+            for (int pl = 0; pl < 2; ++pl)
+                ex.push_back(make_extract<C>(ctx, blks[b].l, blks[b].r == 1, pl, {blks[b].s == 0 ? 0 : chunk},
+                                             T + b * chunk * n2 + pl * ctx.P, n2, ldc, 1.0));
+        rec_extract<C>(ctx, rec, ex, chunk);
+        const dim3 g1(cdiv((long long)chunk * n2, 256)), g2(cdiv((long long)chunk * n2, 256), (unsigned)nb);
+        for (int k0 = 0; k0 < n2; k0 += chunk) {
+            k_unit_traces<<<g1, 256, 0, ctx.stream>>>(U, n2, chunk, k0);
+            HZ_CHECK_LAUNCH();
+            rec.run(ctx.stream);
+            k_store_blocks<C><<<g2, 256, 0, ctx.stream>>>((C*)tb.base, d_off, T, n2, chunk, k0);
+            HZ_CHECK_LAUNCH();
+        }
+        HZ_CUDA(cudaStreamSynchronize(ctx.stream));
+    } catch (...) {
+        cudaStreamSynchronize(ctx.stream);
+        cleanup();
+        cudaFree(tb.base);
+        throw;
+    }
+    cleanup();
+    ctx.tb.release();
+    ctx.tb = tb;
+}
 
 // ------------------------------------------------------------------------------------------
 // operators (recorders)
@@ -719,6 +1070,10 @@ void rec_polarized_rhs(Ctx& ctx, Rec& rec, const double2* g, bool scale, int R, 
 // y = M_pol x: u_down = D_down x_down + U x_up,  u_up = D_up x_up + L x_down.
 template <class C>
 void rec_apply_mpol(Ctx& ctx, Rec& rec, const double2* x, int R, double2* y) {
+    if (use_trace_blocks<C>(ctx, R)) {
+        rec_apply_mpol_blocks<C>(ctx, rec, x, R, y);
+        return;
+    }
     const bool dbl = sizeof(C) == 16;
     const int K = ctx.K, L = ctx.L;
     const long long ntr = ctx.ntr;
@@ -783,6 +1138,10 @@ void rec_apply_mpol(Ctx& ctx, Rec& rec, const double2* x, int R, double2* y) {
 // tmp: one trace vector [R][ntr] of scratch.
 template <class C>
 void rec_apply_precond(Ctx& ctx, Rec& rec, const double2* x, int R, double2* y, double2* tmp) {
+    if (use_trace_blocks<C>(ctx, R)) {
+        rec_apply_precond_blocks<C>(ctx, rec, x, R, y, tmp);
+        return;
+    }
     const bool dbl = sizeof(C) == 16;
     const int K = ctx.K, L = ctx.L;
     const long long ntr = ctx.ntr;
@@ -1196,6 +1555,8 @@ template void op_apply_precond<float2>(Ctx&, const double2*, int, double2*, doub
 template void op_apply_precond<double2>(Ctx&, const double2*, int, double2*, double2*);
 template void op_reconstruct<float2>(Ctx&, const double2*, bool, const double2*, int, double2*, bool);
 template void op_reconstruct<double2>(Ctx&, const double2*, bool, const double2*, int, double2*, bool);
+template void build_trace_blocks<float2>(Ctx&, int);
+template void build_trace_blocks<double2>(Ctx&, int);
 // ------------------------------------------------------------------------------------------
 // Bi-CGSTAB on the same left-preconditioned trace system P M_pol x = P f_pol (the paper's
 // remark on Krylov solvers in its Parallelization Strategies section: Bi-CGSTAB keeps a fixed,

@@ -29,6 +29,7 @@ EXPORTED = [
     "hz_apply_mpol", "hz_apply_precond", "hz_reconstruct", "hz_volume_residual",
     "hz_profile_begin", "hz_profile_begin_detail", "hz_profile_end", "hz_profile_kernel", "hz_profile_report", "hz_kernel_launches", "hz_volume_residual_noalloc",
     "hz_tuning_report", "hz_solve_group", "hz_create_shared", "hz_tensor_peak", "hz_factor_report",
+    "hz_trace_blocks",
 ]
 
 
@@ -98,6 +99,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.hz_create_shared.argtypes = [VP, VP, P(VP)]
     lib.hz_solve_group.argtypes = [P(VP), I32, P(VP), P(I32), P(VP), P(SolveOpts), P(VP), P(ct.c_int)]
     lib.hz_tensor_peak.argtypes = [I32, I32, D, P(D), P(D)]
+    lib.hz_trace_blocks.argtypes = [VP, I32, P(ct.c_int64)]
     lib.hz_factor_report.argtypes = [VP]
     lib.hz_factor_report.restype = ct.c_char_p
     for name in EXPORTED:
@@ -213,6 +215,14 @@ class Solver:
         self._check(st, (HZ_OK, HZ_ERR_NO_CONVERGENCE) if allow_noconv else (HZ_OK,))
         return u, list(info), st
 
+    def trace_blocks(self, max_cols: int = 32) -> int:
+        """Explicit trace-to-trace Green's blocks (hz_trace_blocks): M_pol and the preconditioner
+        use dense block products for solves of at most max_cols right-hand sides; 0 releases the
+        blocks.  Returns the device bytes they hold."""
+        nb = ct.c_int64()
+        self._check(self.lib.hz_trace_blocks(self.h, int(max_cols), ct.byref(nb)))
+        return nb.value
+
     # -------------------------------------------------------------------- introspection
     def layer_info(self, ell: int):
         v = [ct.c_int32() for _ in range(4)]
@@ -308,7 +318,8 @@ class Solver:
         self._check(fn(self.h))
 
     def profile_kernel(self, kind: int):
-        """Per-kernel-kind totals of the last detail-profiled interval: 0 CUDA-core, 1 tensor-core."""
+        """Per-kernel-kind totals of the last detail-profiled interval: 0 CUDA-core, 1 tensor-core
+        substitution, 2 explicit trace-block products."""
         n, ms, by, fl = ct.c_int64(), ct.c_double(), ct.c_double(), ct.c_double()
         self._check(self.lib.hz_profile_kernel(self.h, kind, ct.byref(n), ct.byref(ms), ct.byref(by), ct.byref(fl)))
         return dict(launches=n.value, ms=ms.value, bytes=by.value, flops=fl.value)

@@ -375,8 +375,9 @@ def test_profile_detail_attributes_launches_by_kernel_kind(hz, small_case, monke
     assert tot["calls"] > 0 and k0["launches"] > 0 and k1["launches"] > 0
     assert k0["ms"] > 0 and k1["ms"] > 0
     assert abs(k0["flops"] + k1["flops"] - tot["flops"]) <= 0.05 * tot["flops"]
+    assert s.profile_kernel(2)["launches"] == 0   # no explicit trace blocks on this handle
     with pytest.raises(RuntimeError):
-        s.profile_kernel(2)
+        s.profile_kernel(3)
     s.close()
 
 
