@@ -345,7 +345,7 @@ def run_ours(args):
 
     lines = [kernel_line(kern[0], "k_subst / k_subst64 (CUDA-core substitution)"),
              kernel_line(kern[1], "k_subst_tcp / k_subst_tc (tcgen05 split-TF32 substitution)"),
-             kernel_line(kern[2], "k_trace_block (explicit trace-to-trace block products)")]
+             kernel_line(kern[2], "k_trace_block2 / k_trace_block (explicit trace-to-trace block products)")]
     dom = max(range(3), key=lambda i: kern[i]["ms"])
     d = lines[dom]
     traffic = measured_traffic(d["kernel"], args.config, R)

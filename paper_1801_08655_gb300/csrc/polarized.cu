@@ -306,6 +306,117 @@ __global__ void __launch_bounds__(TB_ROWS) k_trace_block(const TBJob<C>* jobs, i
     }
 }
 
+// Complex64 blocks: each thread owns two adjacent read-out rows (one 16-byte load per source
+// entry) and streams its own rows of E through a private ring of TB2_ST stages x TB2_KG source
+// entries in shared memory with cp.async, so that TB2_ST - 1 stages of loads are in flight while
+// it multiplies the stage that has landed (no block barrier is needed for E: a thread reads only
+// what it copied itself).  The source values are staged per TB_KC entries as in k_trace_block.
+constexpr int TB2_THREADS = 256;
+constexpr int TB2_ROWS = 2 * TB2_THREADS;
+constexpr int TB2_KG = 8;
+constexpr int TB2_ST = 4;
+constexpr size_t tb2_smem(int nc) { return (size_t)TB2_ST * TB2_KG * TB2_THREADS * 16 + (size_t)TB_KC * nc * 8; }
+
+__device__ inline void cp_async16(void* smem_dst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <int NC>
+__global__ void __launch_bounds__(TB2_THREADS, 1) k_trace_block2(const TBJob<float2>* jobs, int n2, int R, long long xs,
+                                                                 long long ys, int kslice, int ncg) {
+    extern __shared__ __align__(16) unsigned char tb2_smem_raw[];
+    float4* ring = reinterpret_cast<float4*>(tb2_smem_raw);   // [TB2_ST][TB2_KG][TB2_THREADS]
+    float2(*xsm)[NC] = reinterpret_cast<float2(*)[NC]>(tb2_smem_raw + (size_t)TB2_ST * TB2_KG * TB2_THREADS * 16);
+    const TBJob<float2>& jb = jobs[blockIdx.z];
+    const int tid = threadIdx.x;
+    const int m = blockIdx.x * TB2_ROWS + 2 * tid;   // rows m and m + 1 (n2 is even)
+    const bool row_ok = m < n2;
+    const int cg = blockIdx.y % ncg, ks = blockIdx.y / ncg;
+    const int c0 = cg * NC;
+    const int kb = ks * kslice, ke = min(n2, kb + kslice);
+    const int G = (ke - kb + TB2_KG - 1) / TB2_KG;   // pipeline stages of this slice (uniform over the block)
+    float2 a0[NC], a1[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) { a0[c] = czero<float2>(); a1[c] = czero<float2>(); }
+    const int nterm = jb.nterm;
+    for (int t = 0; t < nterm; ++t) {
+        const float2* E = jb.t[t].E;
+        const double2* x0 = jb.t[t].x0;
+        const double2* x1 = jb.t[t].x1;
+        auto issue = [&](int g) {   // one commit group per stage
+            const int sl = g % TB2_ST;
+#pragma unroll
+            for (int u = 0; u < TB2_KG; ++u) {
+                const int k = kb + g * TB2_KG + u;
+                float4* dst = ring + (sl * TB2_KG + u) * TB2_THREADS + tid;
+                if (row_ok && k < ke) cp_async16(dst, E + (long long)k * n2 + m);
+                else *dst = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int g = 0; g < TB2_ST - 1; ++g) {
+            if (g < G) issue(g);
+            else cp_async_commit();
+        }
+        for (int g = 0; g < G; ++g) {
+            const int kk0 = (g * TB2_KG) % TB_KC;
+            if (kk0 == 0) {   // next TB_KC source entries of x (all threads reach this together)
+                __syncthreads();
+                const int kc = kb + g * TB2_KG;
+                for (int i = tid; i < TB_KC * NC; i += TB2_THREADS) {
+                    const int kk = i % TB_KC, c = i / TB_KC;
+                    const int k = kc + kk, r = c0 + c;
+                    double2 v = make_double2(0.0, 0.0);
+                    if (k < ke && r < R) {
+                        v = x0[(long long)r * xs + k];
+                        if (x1) v = cadd(v, x1[(long long)r * xs + k]);
+                    }
+                    xsm[kk][c] = to_f(v);
+                }
+                __syncthreads();
+            }
+            if (g + TB2_ST - 1 < G) issue(g + TB2_ST - 1);
+            else cp_async_commit();
+            cp_async_wait<TB2_ST - 1>();   // this thread's copies of stage g have landed
+            const int sl = g % TB2_ST;
+#pragma unroll
+            for (int u = 0; u < TB2_KG; ++u) {
+                const float4 e = ring[(sl * TB2_KG + u) * TB2_THREADS + tid];
+                const float2 e0 = make_float2(e.x, e.y), e1 = make_float2(e.z, e.w);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const float2 xv = xsm[kk0 + u][c];
+                    cfma(a0[c], e0, xv);
+                    cfma(a1[c], e1, xv);
+                }
+            }
+        }
+        cp_async_wait<0>();   // the ring is reused by the next term
+    }
+    if (!row_ok) return;
+    const bool atomic = gridDim.y > (unsigned)ncg;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int r = c0 + c;
+        if (r >= R) break;
+        double2* yp = jb.y + (long long)r * ys + m;
+        const double2 v0 = cscale(to_d(a0[c]), jb.sign), v1 = cscale(to_d(a1[c]), jb.sign);
+        if (atomic) {
+            atomicAdd(&yp[0].x, v0.x);
+            atomicAdd(&yp[0].y, v0.y);
+            atomicAdd(&yp[1].x, v1.x);
+            atomicAdd(&yp[1].y, v1.y);
+        } else {
+            yp[0] = cadd(yp[0], v0);
+            yp[1] = cadd(yp[1], v1);
+        }
+    }
+}
+
 // U[r][k] = (k == k0 + r), r < ncols, k < n2: unit source traces k0 .. k0 + ncols - 1 (pairs
 // flattened as (plane, cell)); columns past the last trace stay zero.
 __global__ void k_unit_traces(double2* U, int n2, int ncols, int k0) {
@@ -824,23 +935,65 @@ void launch_trace_block(const TBJob<C>* d, unsigned njobs, int n2, int R, long l
     HZ_CHECK_LAUNCH();
 }
 
+// k_trace_block2 takes more than the default 48 KiB of dynamic shared memory; set at record time
+// (never inside a stream capture), on the current device
+inline void tb2_allow_smem() {
+    HZ_CUDA(cudaFuncSetAttribute(k_trace_block2<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb2_smem(8)));
+    HZ_CUDA(cudaFuncSetAttribute(k_trace_block2<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb2_smem(16)));
+}
+
+template <int NC>
+void launch_trace_block2(const TBJob<float2>* d, unsigned njobs, int n2, int R, long long xs, long long ys, int ksplit,
+                         int kslice, int ncg, cudaStream_t st) {
+    dim3 grid(cdiv(n2, TB2_ROWS), (unsigned)(ncg * ksplit), njobs);
+    k_trace_block2<NC><<<grid, TB2_THREADS, tb2_smem(NC), st>>>(d, n2, R, xs, ys, kslice, ncg);
+    HZ_CHECK_LAUNCH();
+}
+
+inline void launch_tb_kind(const TBJob<float2>* d, unsigned nj, int n2, int R, long long xs, long long ys, int ksplit,
+                           int kslice, int ncg, int NC, cudaStream_t st) {
+    if (NC == 8) launch_trace_block2<8>(d, nj, n2, R, xs, ys, ksplit, kslice, ncg, st);
+    else launch_trace_block2<16>(d, nj, n2, R, xs, ys, ksplit, kslice, ncg, st);
+}
+inline void launch_tb_kind(const TBJob<double2>* d, unsigned nj, int n2, int R, long long xs, long long ys, int ksplit,
+                           int kslice, int ncg, int NC, cudaStream_t st) {
+    if (NC == 8) launch_trace_block<double2, 8>(d, nj, n2, R, xs, ys, ksplit, kslice, ncg, st);
+    else launch_trace_block<double2, 16>(d, nj, n2, R, xs, ys, ksplit, kslice, ncg, st);
+}
+
 // One launch of block products over independent jobs (distinct outputs), on trace pairs of
-// vectors with the trace-vector stride.  Outputs must hold their other terms already.  Enough
-// K slices are used to give the GPU about two blocks per SM.
+// vectors with the trace-vector stride.  Outputs must hold their other terms already.  The source
+// range is split into K slices (partial sums added with FP64 atomics) when that fills the GPU's
+// block slots with less wave quantization.
 template <class C>
 void rec_trace_blocks(Ctx& ctx, Rec& rec, const std::vector<TBJob<C>>& jobs, int R) {
     if (jobs.empty()) return;
     const bool dbl = sizeof(C) == 16;
     const int n2 = (int)(2 * ctx.P);
-    const int NC = (R <= 8) ? 8 : (dbl || R <= 16) ? 16 : 32;
+    // complex64: k_trace_block2 with 8 or 16 columns per pass; complex128: k_trace_block
+    const int NC = R <= 8 ? 8 : 16;
     const int ncg = cdiv(R, NC);
+    const int rows = dbl ? TB_ROWS : TB2_ROWS;
     int sms = 0;
     HZ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx.device));
-    const long long base = (long long)cdiv(n2, TB_ROWS) * ncg * (long long)jobs.size();
-    int ksplit = (int)std::max<long long>(1, std::min<long long>((2LL * sms) / std::max<long long>(1, base),
-                                                                 std::max(1, n2 / (4 * TB_KC))));
+    // resident blocks per launch: k_trace_block2 one per SM (210 registers x 256 threads), k_trace_block two
+    const long long slots = (dbl ? 2LL : 1LL) * sms;
+    const long long base = (long long)cdiv(n2, rows) * ncg * (long long)jobs.size();
+    const int kmax = std::max(1, n2 / (4 * TB_KC));
+    // smallest split whose blocks fill at least 90 % of the slots of their last wave, else the best one
+    int ksplit = 1;
+    double best = -1.0;
+    for (int k = 1; k <= kmax; ++k) {
+        const int ksl = cdiv(cdiv(n2, k), TB_KC) * TB_KC;
+        const long long blocks = base * cdiv(n2, ksl);
+        const double waves = (double)blocks / slots;
+        const double eff = blocks < slots ? waves : waves / std::ceil(waves);
+        if (eff > best + 1e-9) { best = eff; ksplit = k; }
+        if (eff >= 0.9) break;
+    }
     const int kslice = cdiv(cdiv(n2, ksplit), TB_KC) * TB_KC;
     ksplit = cdiv(n2, kslice);
+    if (!dbl) tb2_allow_smem();
     const TBJob<C>* d = rec.up(jobs);
     const unsigned nj = (unsigned)jobs.size();
     const long long xs = ctx.ntr, ys = ctx.ntr;
@@ -858,9 +1011,7 @@ void rec_trace_blocks(Ctx& ctx, Rec& rec, const std::vector<TBJob<C>>& jobs, int
             HZ_CUDA(cudaEventCreate(&pr.e1));
             HZ_CUDA(cudaEventRecord(pr.e0, st));
         }
-        if (NC == 8) launch_trace_block<C, 8>(d, nj, n2, R, xs, ys, ksplit, kslice, ncg, st);
-        else if (NC == 16) launch_trace_block<C, 16>(d, nj, n2, R, xs, ys, ksplit, kslice, ncg, st);
-        else launch_trace_block<C, (sizeof(C) == 16 ? 16 : 32)>(d, nj, n2, R, xs, ys, ksplit, kslice, ncg, st);
+        launch_tb_kind(d, nj, n2, R, xs, ys, ksplit, kslice, ncg, NC, st);
         if (timed) {
             HZ_CUDA(cudaEventRecord(pr.e1, st));
             pr.kind = 2;
