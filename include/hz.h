@@ -255,9 +255,11 @@ hz_status hz_apply_mpol(hz_handle* h, const double* x, int32_t R, double* y);
 hz_status hz_apply_precond(hz_handle* h, const double* x, int32_t R, double* y);
 
 /*
- * hz_trace_blocks -- explicit trace-to-trace Green's blocks (Local Solves section: with selective
- * inversion, thin layers can keep the local Green's function between their interface plane pairs
- * explicitly instead of running a forward and backward substitution per application).  For every
+ * hz_trace_blocks -- explicit trace-to-trace Green's blocks.  The paper applies the blocks of the SIE
+ * and polarized matrices only matrix-free, by local solves with interface sources (Reduction to a
+ * surface integral equation section, Algorithms 4-9: in 3D the matrix is never formed), and cites
+ * selective inversion (Local Solves section) for trading factor storage for dense products; this
+ * entry point takes that trade one step further on problems small enough for it.  For every
  * layer it computes the dense 2P x 2P blocks E_rs (P = nx*ny) taking a trace pair on the layer's
  * top or bottom interface s, through that interface's source, to the layer's top or bottom
  * read-out pair r: 4L - 6 blocks, one local solve per unit source trace, in the precision of the
@@ -270,7 +272,7 @@ hz_status hz_apply_precond(hz_handle* h, const double* x, int32_t R, double* y);
  *   bytes     may be NULL; receives the device bytes the blocks hold
  * The blocks are owned by the handle (released by hz_destroy, by hz_trace_blocks(h, 0, ...), and by
  * hz_factor, after which they must be built again); handles from hz_create_shared have their own.
- * Memory: (4L - 6) * 4 P^2 complex elements, 14 GiB at 64^3 with 8 layers in complex64 -- the
+ * Memory: (4L - 6) * 4 P^2 complex elements, 14.0 GB at 64^3 with 8 layers in complex64 -- the
  * blocks pay where layers are thin and right-hand sides few; at 128^3 they do not fit.
  * Errors: HZ_ERR_ARG (max_cols < 0), HZ_ERR_STATE (not factored), HZ_ERR_OOM / HZ_ERR_ADMISSION
  * (blocks or the build's workspace do not fit; the handle is left without blocks), HZ_ERR_CUDA.

@@ -31,9 +31,9 @@ in tests/test_oracle_polarized.py against the global direct solve):
 * Algorithm 9 (U) is the mirror image of Algorithm 6: for layer ell, the
   local field due to both of its interfaces' up-going traces, read on its
   bottom pair, minus the input on plane P.
-* Explicit trace-to-trace blocks (trace_blocks): the Local Solves section names them
-  (selective inversion for thin layers) without giving their form; they are read as the local
-  Green's function between the interface pairs, R_rd G^ell R_src^T J_src, with J_src the
+* Explicit trace-to-trace blocks (trace_blocks): the paper applies the blocks of its trace
+  operators only matrix-free (never forming the SIE matrix in 3D); written out, a block is the
+  local Green's function between two interface pairs, R_rd G^ell R_src^T J_src, with J_src the
   interface source's weights, which makes E_rs J_s^{-1} = (E_sr J_r^{-1})^T by the complex
   symmetry of the local operator (pinned).
 * The polarized right-hand side after "algebraic operations and permutations"
@@ -253,9 +253,9 @@ class PolarizedModel:
 
     # ------------------------------------------------------------------ explicit trace blocks
     def trace_blocks(self):
-        """Explicit trace-to-trace Green's blocks of every layer (the Local Solves section: with
-        selective inversion the local Green's functions restricted to the interfaces can be kept
-        explicitly for thin layers, instead of a pair of triangular solves per application).
+        """Explicit trace-to-trace Green's blocks of every layer: the local Green's function
+        between the layer's interface plane pairs, i.e. the blocks that Algorithms 4-9 apply
+        matrix-free by local solves with interface sources, written out as dense matrices.
 
         Returns a list over layers of dicts: E[ell][rd + src] with rd, src in {'t', 'b'} is the
         dense (2P x 2P) matrix taking a trace pair on the layer's top interface (src 't', interface

@@ -217,8 +217,8 @@ __global__ void k_pairs_axpy(double2* y, long long ystride, const double2* x, lo
 
 
 // ------------------------------------------------------------------------------------------
-// explicit trace-to-trace Green's blocks (the Local Solves section: selective inversion lets
-// thin layers keep the local Green's function between their interface pairs explicitly)
+// explicit trace-to-trace Green's blocks: the local Green's function between a layer's interface
+// plane pairs (the blocks Algorithms 4-9 apply matrix-free by local solves), stored densely
 // ------------------------------------------------------------------------------------------
 // One term of a block product: E (2P x 2P, column-major, complex type C) applied to the trace
 // pair x0 (+ x1 when given), each pair [r * xstride + k], k < 2P.

@@ -1,5 +1,5 @@
-"""Pins of the oracle's explicit trace-to-trace Green's blocks (the Local Solves section: the local
-Green's functions restricted to the interface planes, kept explicitly for thin layers).
+"""Pins of the oracle's explicit trace-to-trace Green's blocks: the local Green's functions between
+the interface plane pairs, i.e. the blocks that Algorithms 4-9 apply matrix-free, written out.
 
 A block E_rs of layer ell maps a trace pair on the layer's interface s (top 't' / bottom 'b')
 through that interface's source to the read-out pair at r.  It is pinned by:
