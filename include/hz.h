@@ -233,7 +233,7 @@ hz_status hz_factor_stats(const hz_handle* h, int64_t* nodes, int64_t* factor_en
 hz_status hz_layer_solve_cost(const hz_handle* h, int32_t ell, double* bytes, double* flops_per_col);
 
 /*
- * Local solve (Algorithm 2, "solve local problems"): w = (H^ell)^{-1} g for ncols
+ * Local solve (Algorithm 2, its local solves): w = (H^ell)^{-1} g for ncols
  * columns on layer ell's extended local grid of nzl = zhi-zlo+1 planes.
  *   g, w  device, complex arrays [ncols][nzl][ny][nx] (natural local order)
  */

@@ -36,8 +36,8 @@ in tests/test_oracle_polarized.py against the global direct solve):
   local Green's function between two interface pairs, R_rd G^ell R_src^T J_src, with J_src the
   interface source's weights, which makes E_rs J_s^{-1} = (E_sr J_r^{-1})^T by the complex
   symmetry of the local operator (pinned).
-* The polarized right-hand side after "algebraic operations and permutations"
-  (Polarization subsection, not printed): f_down_j = -(v^j(P_j), v^j(Q_j)),
+* The polarized right-hand side, which the paper obtains from the SIE right-hand side by
+  rearrangements it does not print (Polarization subsection): f_down_j = -(v^j(P_j), v^j(Q_j)),
   f_up_j = -(v^{j+1}(P_j), v^{j+1}(Q_j)), with v^ell the local solution for the
   layer's own part of the source (Algorithm 2, local solves).
 """
