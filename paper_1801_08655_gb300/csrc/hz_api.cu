@@ -917,9 +917,11 @@ hz_status hz_solve_group(hz_handle* const* hs, int32_t n, const double* const* r
                          double* const* u, const hz_solve_opts* opts, hz_solve_info* const* info,
                          hz_status* statuses) {
     if (!hs || n < 1 || !rhs || !R || !u) return HZ_ERR_ARG;
-    for (int i = 0; i < n; ++i)
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i]) return HZ_ERR_ARG;
         for (int j = 0; j < i; ++j)
-            if (hs[i] == hs[j] || !hs[i]) return HZ_ERR_ARG;  // a handle is not shared between threads
+            if (hs[i] == hs[j]) return HZ_ERR_ARG;  // a handle is not shared between threads
+    }
     std::vector<hz_status> st(n, HZ_OK);
     std::vector<std::thread> th;
     th.reserve(n);
