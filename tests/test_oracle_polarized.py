@@ -10,7 +10,7 @@ iteration count in the paper's observed range (4-6 per its tables).
 import numpy as np
 import pytest
 
-from oracle import direct, polarized
+from oracle import direct, discretization as D, polarized
 from paper_1801_08655_gb300 import workloads as W
 
 
@@ -110,3 +110,30 @@ def test_two_layers_diagonal_blocks_are_minus_identity():
     x = rng.standard_normal(M.zeros_trace().shape) + 0j
     np.testing.assert_array_equal(M.apply_Dd(x), -x)
     np.testing.assert_array_equal(M.apply_Du(x), -x)
+
+
+def test_exact_green_reductive_case():
+    """The reductive case of the Physical intuition subsection: with the local Green's function
+    equal to the global one (every layer's local solve replaced by the global direct solve, the
+    interface sources and read-outs unchanged), the down-going field has no interface reflections
+    (L y_down = 0 to rounding: reflections arise only from truncating the layers) and the
+    preconditioned GMRES converges in at most the two iterations the paper states, to the direct
+    solution, while the unpreconditioned system needs more.  A dropped identity term in L, for one,
+    leaves L y_down at O(1)."""
+    n, L = 16, 4
+    p = W.small_problem(n, 3, L, seed=5, R=1)
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal((n, n, n)) + 1j * rng.standard_normal((n, n, n))
+    u = direct.solve(p.m, p.omega, p.npml, p.C, f[None])[0]
+    M = polarized.PolarizedModel(p.m, p.omega, p.npml, p.C, L)
+    G = direct.GlobalSolver(D.global_operator(p.m, p.omega, p.npml, p.C), (n, n, n))
+    M.grids = [(0, n - 1)] * L
+    M.solvers = [G] * L
+    fd, fu = M.polarized_rhs(f)
+    yd = M.sweep_down(fd)
+    assert np.linalg.norm(M.apply_L(yd)) <= 1e-12 * np.linalg.norm(yd)
+    us, its = M.solve(f, tol=1e-12)
+    assert its <= 2
+    assert np.linalg.norm(us - u) / np.linalg.norm(u) < 1e-12
+    M.apply_P = lambda rd, ru: (rd, ru)
+    assert M.solve_traces(f, tol=1e-12)[1] > 2
