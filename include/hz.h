@@ -42,7 +42,7 @@ extern "C" {
 typedef enum {
     HZ_OK = 0,
     HZ_ERR_ARG = 1,            /* invalid argument (sizes, null pointers, omega <= 0, ...) */
-    HZ_ERR_OOM = 2,            /* device allocation failed */
+    HZ_ERR_OOM = 2,            /* device memory exhausted (other allocation failures are HZ_ERR_CUDA) */
     HZ_ERR_ADMISSION = 3,      /* request does not fit in the free device memory */
     HZ_ERR_STATE = 4,          /* call out of order (e.g. solve before factor) */
     HZ_ERR_NONFINITE = 5,      /* NaN/Inf in m, rhs or a result */
@@ -103,7 +103,7 @@ void hz_default_opts(hz_precision prec, hz_solve_opts* opts);
  *   omega     angular frequency > 0
  *   pml       PML parameters (see hz_pml)
  *   n_layers  number of slabs L, 1 <= L <= number of physical z planes
- *   prec      HZ_PREC_FP64 or HZ_PREC_MIXED
+ *   prec      HZ_PREC_FP64, HZ_PREC_MIXED or HZ_PREC_MIXED_FP64_FACTOR
  *   stream    cudaStream_t to queue work on (0 for the default stream)
  *   out       receives the new handle (NULL on failure)
  * Errors: HZ_ERR_ARG, HZ_ERR_NONFINITE (m), HZ_ERR_OOM, HZ_ERR_CUDA.

@@ -58,22 +58,28 @@ double2 inv_s(double sigma, double omega) {
     return make_double2(v.real(), v.imag());
 }
 
+// A failed cudaMalloc is HZ_ERR_OOM when the device ran out of memory and HZ_ERR_CUDA otherwise
+// (no device, driver missing, a sticky error from earlier work), with the runtime's message.
+[[noreturn]] void alloc_failed(cudaError_t e, size_t bytes) {
+    cudaGetLastError();
+    const std::string what = "device allocation of " + std::to_string(bytes) + " bytes failed: ";
+    if (e == cudaErrorMemoryAllocation) throw Error{HZ_ERR_OOM, what + cudaGetErrorString(e)};
+    throw Error{HZ_ERR_CUDA, what + cudaGetErrorString(e)};
+}
+
 template <class T> T* dev_copy(const std::vector<T>& v) {
     T* d = nullptr;
-    if (cudaMalloc(&d, std::max<size_t>(1, v.size()) * sizeof(T)) != cudaSuccess) {
-        cudaGetLastError();
-        throw Error{HZ_ERR_OOM, "device allocation failed"};
-    }
+    const size_t bytes = std::max<size_t>(1, v.size()) * sizeof(T);
+    const cudaError_t e = cudaMalloc(&d, bytes);
+    if (e != cudaSuccess) alloc_failed(e, bytes);
     HZ_CUDA(cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
     return d;
 }
 
 void* dev_alloc(size_t bytes) {
     void* d = nullptr;
-    if (cudaMalloc(&d, std::max<size_t>(bytes, 16)) != cudaSuccess) {
-        cudaGetLastError();
-        throw Error{HZ_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed"};
-    }
+    const cudaError_t e = cudaMalloc(&d, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) alloc_failed(e, bytes);
     return d;
 }
 

@@ -81,3 +81,13 @@ def test_group_solve_rejects_missing_handles(lib):
     assert lib.hz_solve_group(hs, 2, rp, Rs, rp, None, None, sts) == hz.HZ_ERR_ARG
     assert lib.hz_solve_group(None, 1, rp, Rs, rp, None, None, sts) == hz.HZ_ERR_ARG
     assert lib.hz_solve_group(hs, 0, rp, Rs, rp, None, None, sts) == hz.HZ_ERR_ARG
+
+
+def test_create_without_a_device_is_a_cuda_status(lib):
+    """With valid arguments but no usable GPU the first device allocation fails: a status
+    (HZ_ERR_CUDA, not HZ_ERR_OOM: nothing ran out of memory) with the runtime's reason."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    st, out, msg = _create(lib)
+    assert st == hz.HZ_ERR_CUDA and out is None and "allocation" in msg
