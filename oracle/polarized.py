@@ -171,6 +171,39 @@ class PolarizedModel:
             u[lo:hi + 1] = w[lo - zlo:hi - zlo + 1]
         return u
 
+    # ------------------------------------------------------------------ SIE matrix (Algorithm 3)
+    def sie_rhs(self, f):
+        """Right-hand side of the SIE as Algorithm 2 forms it: for interface j, the local fields of
+        the two layers at the interface's planes, (v^j(P_j), v^{j+1}(Q_j))."""
+        v = self.local_fields(f)
+        out = self.zeros_trace()
+        for j in range(self.K):
+            P = self.parts[j][1]
+            out[j] = np.stack([self.plane(j, v[j], P), self.plane(j + 1, v[j + 1], P + 1)])
+        return out
+
+    def apply_M(self, t):
+        """Application of the SIE matrix (Algorithm 3), matrix-free: every layer's local solve with
+        the interface sources of the traces on both of its interfaces, read on the layer's own
+        boundary planes, minus the input there: (M t)_j = (w^j(P_j) - t_j(P), w^{j+1}(Q_j) - t_j(Q)).
+        Read as G1 (the layer-2 source of the first step is v^2_1, the first output is u^1 at plane
+        n^1).  With the interface weights of the assembled matrix (R7) the exact traces solve
+        M t = -sie_rhs(f): the Green's representation formula gives t = v + w(t) on those planes."""
+        K, L = self.K, self.L
+        out = self.zeros_trace()
+        w = []
+        for ell in range(L):
+            g = self.zeros_local(ell)
+            if ell >= 1:
+                self.S_top(ell, t[ell - 1], g)
+            if ell <= L - 2:
+                self.S_bot(ell, t[ell], g)
+            w.append(self.local_solve(ell, g))
+        for j in range(K):
+            P = self.parts[j][1]
+            out[j] = np.stack([self.plane(j, w[j], P) - t[j][0], self.plane(j + 1, w[j + 1], P + 1) - t[j][1]])
+        return out
+
     # ------------------------------------------------------------------ blocks of M_pol
     def apply_Mpol(self, xd, xu):
         """Application of the polarized matrix (appendix): u_d = D_d x_d + U x_u,

@@ -9,6 +9,7 @@ iteration count in the paper's observed range (4-6 per its tables).
 """
 import numpy as np
 import pytest
+import scipy.sparse.linalg as spla
 
 from oracle import direct, discretization as D, polarized
 from paper_1801_08655_gb300 import workloads as W
@@ -137,3 +138,24 @@ def test_exact_green_reductive_case():
     assert np.linalg.norm(us - u) / np.linalg.norm(u) < 1e-12
     M.apply_P = lambda rd, ru: (rd, ru)
     assert M.solve_traces(f, tol=1e-12)[1] > 2
+
+
+def test_exact_traces_solve_the_sie(case):
+    """The SIE reduction (Reduction to a surface integral equation section; Algorithms 2-3): the
+    traces of the global solution solve M t = -f_SIE, f_SIE the local fields at the interface
+    planes as Algorithm 2 forms them (the sign of reading G2); GMRES on M, matrix-free and
+    unpreconditioned, reaches the same traces, and the reconstruction from them is the global
+    solution.  The polarized unknowns sum to those traces as well."""
+    p, f, u, M = case
+    t = M.traces_of(u)
+    b = -M.sie_rhs(f)
+    r = M.apply_M(t) - b
+    assert np.linalg.norm(r) <= 1e-12 * np.linalg.norm(b)
+    n = t.size
+    op = spla.LinearOperator((n, n), matvec=lambda x: M.apply_M(x.reshape(t.shape)).ravel(), dtype=np.complex128)
+    x, info = spla.gmres(op, b.ravel(), rtol=1e-12, atol=0.0, restart=200, maxiter=400)
+    assert info == 0
+    assert np.linalg.norm(x - t.ravel()) <= 1e-9 * np.linalg.norm(t)
+    assert np.linalg.norm(M.reconstruct(f, x.reshape(t.shape)) - u) <= 1e-9 * np.linalg.norm(u)
+    ts, _ = M.solve_traces(f, tol=1e-12)
+    assert np.linalg.norm(ts - t) <= 1e-9 * np.linalg.norm(t)
