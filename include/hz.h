@@ -255,6 +255,27 @@ hz_status hz_apply_mpol(hz_handle* h, const double* x, int32_t R, double* y);
 hz_status hz_apply_precond(hz_handle* h, const double* x, int32_t R, double* y);
 
 /*
+ * hz_symbolic_shape -- the symbolic phase that hz_create runs for every distinct slab shape,
+ * on its own: the nested-dissection reordering of the Local Solves section, here geometric
+ * (recursive bisection of the box by one-cell planes down to leaf boxes of at most `leaf`
+ * cells), with every tree node's own unknowns and update set.  Host code only: needs no GPU.
+ *   nx, ny, nz  box sizes (>= 1, at most 2^30 cells); leaf: largest leaf box in cells (>= 1)
+ *   n_nodes, n_upd   receive the node count and the total length of the update sets
+ *   perm        int32[nx*ny*nz] or NULL: elimination index -> natural cell (z*ny + y)*nx + x
+ *   own0, nown, parent   int32[n_nodes] or NULL: node k owns elimination indices
+ *               [own0[k], own0[k] + nown[k]); parent[k] = -1 at the root; nodes are in
+ *               post-order (children before parents), so a subtree's unknowns are contiguous
+ *   upd_off     int64[n_nodes] or NULL, upd_idx int32[n_upd] or NULL: node k's update set is
+ *               upd_idx[upd_off[k] .. upd_off[k] + (its length)), sorted elimination indices;
+ *               lengths follow from upd_off and n_upd in node order
+ * Call once with NULL arrays for the counts, then with caller-owned arrays of those sizes.
+ * Errors: HZ_ERR_ARG (sizes), HZ_ERR_OOM (host memory); hz_last_error(NULL) explains.
+ */
+hz_status hz_symbolic_shape(int32_t nx, int32_t ny, int32_t nz, int32_t leaf, int64_t* n_nodes, int64_t* n_upd,
+                            int32_t* perm, int32_t* own0, int32_t* nown, int32_t* parent, int64_t* upd_off,
+                            int32_t* upd_idx);
+
+/*
  * hz_trace_blocks -- explicit trace-to-trace Green's blocks.  The paper applies the blocks of the SIE
  * and polarized matrices only matrix-free, by local solves with interface sources (Reduction to a
  * surface integral equation section, Algorithms 4-9: in 3D the matrix is never formed), and cites

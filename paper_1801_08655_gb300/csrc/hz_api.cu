@@ -693,6 +693,35 @@ hz_status hz_trace_blocks(hz_handle* h, int32_t max_cols, int64_t* bytes) {
     })
 }
 
+hz_status hz_symbolic_shape(int32_t nx, int32_t ny, int32_t nz, int32_t leaf, int64_t* n_nodes, int64_t* n_upd,
+                            int32_t* perm, int32_t* own0, int32_t* nown, int32_t* parent, int64_t* upd_off,
+                            int32_t* upd_idx) {
+    try {
+        if (nx < 1 || ny < 1 || nz < 1 || leaf < 1 || (long long)nx * ny * nz > (1LL << 30))
+            throw Error{HZ_ERR_ARG, "hz_symbolic_shape: box sizes or leaf out of range"};
+        Shape sh;
+        build_shape(sh, nx, ny, nz, leaf);
+        if (n_nodes) *n_nodes = (int64_t)sh.nodes.size();
+        if (n_upd) *n_upd = (int64_t)sh.upd_idx.size();
+        if (perm) std::memcpy(perm, sh.perm.data(), sh.perm.size() * sizeof(int32_t));
+        for (size_t i = 0; i < sh.nodes.size(); ++i) {
+            const Node& nd = sh.nodes[i];
+            if (own0) own0[i] = nd.own0;
+            if (nown) nown[i] = nd.nown;
+            if (parent) parent[i] = nd.parent;
+            if (upd_off) upd_off[i] = nd.upd_off;
+        }
+        if (upd_idx) std::memcpy(upd_idx, sh.upd_idx.data(), sh.upd_idx.size() * sizeof(int32_t));
+        return HZ_OK;
+    } catch (const Error& e) {
+        g_create_error = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc&) {
+        g_create_error = "host allocation failed";
+        return HZ_ERR_OOM;
+    }
+}
+
 const char* hz_last_error(const hz_handle* h) {
     if (!h) return g_create_error.c_str();
     return h->ctx.last_error.c_str();

@@ -29,7 +29,7 @@ EXPORTED = [
     "hz_apply_mpol", "hz_apply_precond", "hz_reconstruct", "hz_volume_residual",
     "hz_profile_begin", "hz_profile_begin_detail", "hz_profile_end", "hz_profile_kernel", "hz_profile_report", "hz_kernel_launches", "hz_volume_residual_noalloc",
     "hz_tuning_report", "hz_solve_group", "hz_create_shared", "hz_tensor_peak", "hz_factor_report",
-    "hz_trace_blocks",
+    "hz_trace_blocks", "hz_symbolic_shape",
 ]
 
 
@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.hz_solve_group.argtypes = [P(VP), I32, P(VP), P(I32), P(VP), P(SolveOpts), P(VP), P(ct.c_int)]
     lib.hz_tensor_peak.argtypes = [I32, I32, D, P(D), P(D)]
     lib.hz_trace_blocks.argtypes = [VP, I32, P(ct.c_int64)]
+    lib.hz_symbolic_shape.argtypes = [I32, I32, I32, I32, P(ct.c_int64), P(ct.c_int64), VP, VP, VP, VP, VP, VP]
     lib.hz_factor_report.argtypes = [VP]
     lib.hz_factor_report.restype = ct.c_char_p
     for name in EXPORTED:
@@ -370,6 +371,24 @@ def tensor_peak(kind: str = "tf32", n: int = 128, seconds: float = 1.0):
     if st != HZ_OK:
         raise HzError(st, f"hz_tensor_peak({kind}, {n}) failed")
     return tf.value, ms.value
+
+
+def symbolic_shape(nx: int, ny: int, nz: int, leaf: int = 256):
+    """The library's nested-dissection symbolic phase of one box shape (hz_symbolic_shape, host
+    only): dict of perm, own0, nown, parent, upd_off and upd_idx as numpy arrays."""
+    lib = load()
+    nn, nu = ct.c_int64(), ct.c_int64()
+    st = lib.hz_symbolic_shape(nx, ny, nz, leaf, ct.byref(nn), ct.byref(nu), None, None, None, None, None, None)
+    if st != HZ_OK:
+        raise HzError(st, lib.hz_last_error(None).decode())
+    out = dict(perm=np.empty(nx * ny * nz, np.int32), own0=np.empty(nn.value, np.int32),
+               nown=np.empty(nn.value, np.int32), parent=np.empty(nn.value, np.int32),
+               upd_off=np.empty(nn.value, np.int64), upd_idx=np.empty(nu.value, np.int32))
+    st = lib.hz_symbolic_shape(nx, ny, nz, leaf, ct.byref(nn), ct.byref(nu),
+                               *[out[k].ctypes.data for k in ("perm", "own0", "nown", "parent", "upd_off", "upd_idx")])
+    if st != HZ_OK:
+        raise HzError(st, lib.hz_last_error(None).decode())
+    return out
 
 
 def kernel_launches() -> int:
