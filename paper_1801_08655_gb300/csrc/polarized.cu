@@ -238,6 +238,7 @@ template <class C> struct TBJob {
 constexpr int TB_ROWS = 256;   // output rows (read-out entries) per block, one per thread
 constexpr int TB_KC = 64;      // source entries staged per step
 
+// Complex128 blocks (complex64 ones go through k_trace_block2 below).
 // Each thread owns one read-out entry m and NC right-hand-side columns; the block streams the
 // columns of E (one unit source trace's read-outs are contiguous, so a warp reads 32 consecutive
 // entries of a column per step) against the source values of TB_KC entries x NC columns staged in
