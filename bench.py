@@ -247,8 +247,11 @@ def run_ours(args):
     if args.trace_blocks > 0:
         # explicit trace-to-trace Green's blocks: M_pol and the preconditioner as block products
         t0 = time.perf_counter()
-        tb_bytes = s.trace_blocks(args.trace_blocks)
-        tblocks = {"max_cols": args.trace_blocks, "bytes": tb_bytes, "build_s": time.perf_counter() - t0}
+        try:
+            tb_bytes = s.trace_blocks(args.trace_blocks)
+            tblocks = {"max_cols": args.trace_blocks, "bytes": tb_bytes, "build_s": time.perf_counter() - t0}
+        except hz.HzError as e:   # e.g. blocks larger than the free device memory: local solves
+            tblocks = {"max_cols": args.trace_blocks, "error": str(e)}
     with torch.cuda.stream(stream):
         rhs = torch.zeros((R, n, n, n), dtype=torch.complex128, device=dev)
         for r, (z, y, x) in enumerate(src):
@@ -475,7 +478,7 @@ def run_ours(args):
                        if args.config == 3 else
                        (f"{W.CONFIG_NAMES[args.config]}{' with smooth random density 1..2.5' if args.density else ''} "
                         f"(solved with R={R}), mixed precision"
-                        f"{', M_pol and P by explicit trace-to-trace blocks' if tblocks else ''}"),
+                        f"{', M_pol and P by explicit trace-to-trace blocks' if tblocks and 'bytes' in tblocks else ''}"),
                        "n": n, "layers": p.n_layers, "R": R, "precision": "mixed",
                        "trace_blocks": tblocks,
                        "l2": ("inputs larger than L2: ~40 GB of factors streamed every GMRES iteration"
