@@ -194,10 +194,11 @@ class Solver:
     def solve(self, rhs, opts: Optional[SolveOpts] = None, u=None, allow_noconv: bool = False):
         """rhs: complex128 CUDA tensor (R, nz, ny, nx).  Returns (u, [SolveInfo]*R, status)."""
         import torch
-        assert rhs.is_cuda and rhs.dtype == torch.complex128 and rhs.is_contiguous()
+        self._check_volume(rhs)
         R = rhs.shape[0]
         if u is None:
             u = torch.empty_like(rhs)
+        self._check_volume(rhs, u)
         info = (SolveInfo * R)()
         st = self.lib.hz_solve(self.h, _ptr(rhs), R, _ptr(u), ct.byref(opts) if opts else None, info)
         self._check(st, (HZ_OK, HZ_ERR_NO_CONVERGENCE) if allow_noconv else (HZ_OK,))
@@ -207,9 +208,14 @@ class Solver:
                    allow_noconv: bool = False):
         """Host (numpy complex128) rhs and u: the end-to-end entry point."""
         rhs = np.ascontiguousarray(rhs, dtype=np.complex128)
+        if rhs.ndim != 4 or tuple(rhs.shape[1:]) != self.shape:
+            raise ValueError(f"expected rhs of shape (R,) + {self.shape}, got {rhs.shape}")
         R = rhs.shape[0]
         if u is None:
             u = np.empty_like(rhs)
+        if not (isinstance(u, np.ndarray) and u.dtype == np.complex128 and u.flags.c_contiguous
+                and u.shape == rhs.shape):
+            raise ValueError(f"u must be a C-contiguous complex128 array of shape {rhs.shape}")
         info = (SolveInfo * R)()
         st = self.lib.hz_solve_host(self.h, rhs.ctypes.data, R, u.ctypes.data,
                                     ct.byref(opts) if opts else None, info)
@@ -247,7 +253,11 @@ class Solver:
     def layer_solve(self, ell: int, g):
         """g: complex128 CUDA tensor (ncols, nzl, ny, nx) on layer ell's local grid."""
         import torch
-        assert g.is_cuda and g.dtype == torch.complex128 and g.is_contiguous()
+        lo, hi, zlo, zhi = self.layer_info(ell)
+        nz, ny, nx = self.shape
+        if not (g.is_cuda and g.dtype == torch.complex128 and g.is_contiguous() and g.dim() == 4
+                and tuple(g.shape[1:]) == (zhi - zlo + 1, ny, nx)):
+            raise ValueError(f"expected a contiguous complex128 CUDA tensor of shape (ncols, {zhi - zlo + 1}, {ny}, {nx})")
         w = torch.empty_like(g)
         self._check(self.lib.hz_layer_solve(self.h, ell, _ptr(g), g.shape[0], _ptr(w)))
         return w
@@ -256,8 +266,15 @@ class Solver:
         nz, ny, nx = self.shape
         return (R, 2, self.K, 2, ny, nx)
 
+    def _check_traces(self, x, shape):
+        import torch
+        if not (x.is_cuda and x.dtype == torch.complex128 and x.is_contiguous() and tuple(x.shape) == tuple(shape)):
+            raise ValueError(f"expected a contiguous complex128 CUDA tensor of shape {tuple(shape)}, "
+                             f"got {tuple(x.shape)} {x.dtype} on {x.device}")
+
     def polarized_rhs(self, rhs):
         import torch
+        self._check_volume(rhs)
         R = rhs.shape[0]
         out = torch.empty(self.trace_shape(R), dtype=torch.complex128, device=rhs.device)
         self._check(self.lib.hz_polarized_rhs(self.h, _ptr(rhs), R, _ptr(out)))
@@ -265,18 +282,24 @@ class Solver:
 
     def apply_mpol(self, x):
         import torch
+        self._check_traces(x, self.trace_shape(x.shape[0]))
         y = torch.empty_like(x)
         self._check(self.lib.hz_apply_mpol(self.h, _ptr(x), x.shape[0], _ptr(y)))
         return y
 
     def apply_precond(self, x):
         import torch
+        self._check_traces(x, self.trace_shape(x.shape[0]))
         y = torch.empty_like(x)
         self._check(self.lib.hz_apply_precond(self.h, _ptr(x), x.shape[0], _ptr(y)))
         return y
 
     def reconstruct(self, rhs, t):
         import torch
+        self._check_volume(rhs)
+        nz, ny, nx = self.shape
+        if t is not None or self.K > 0:      # one layer has no traces: t may be None
+            self._check_traces(t, (rhs.shape[0], self.K, 2, ny, nx))
         u = torch.empty_like(rhs)
         self._check(self.lib.hz_reconstruct(self.h, _ptr(rhs), _ptr(t), rhs.shape[0], _ptr(u)))
         return u
@@ -354,8 +377,8 @@ def solve_group(solvers, rhs_list, opts: Optional[SolveOpts] = None, allow_nocon
     Rs = (ct.c_int32 * n)(*[r.shape[0] for r in rhs_list])
     ip = (ct.c_void_p * n)(*[ct.addressof(i) for i in infos])
     sts = (ct.c_int * n)()
-    for r in rhs_list:
-        assert r.is_cuda and r.dtype == torch.complex128 and r.is_contiguous()
+    for sv, r in zip(solvers, rhs_list):
+        sv._check_volume(r)
     st = lib.hz_solve_group(hs, n, rp, Rs, up, ct.byref(opts) if opts else None, ip, sts)
     ok = (HZ_OK, HZ_ERR_NO_CONVERGENCE) if allow_noconv else (HZ_OK,)
     if st not in ok:
