@@ -114,3 +114,28 @@ def test_a_second_serve_restarts_the_admitted_workers(monkeypatch):
     srv.serve([], realtime=False, timeout=0.0)
     srv.serve([], realtime=False, timeout=0.0)
     assert len(srv.workers[0]) == 1 and started == [(0, srv.primaries[0])] * 3
+
+
+def test_requests_are_cut_into_column_items_and_batched_in_arrival_order(monkeypatch):
+    """A request of R sources becomes work items of at most max_cols columns; a free worker takes
+    items from the head of its frequency's queue, in arrival order, while they fit in one batch of
+    max_cols columns (items of different requests share a batch)."""
+    srv = make_server(free_bytes=100 * GB, need_bytes=1 * GB, monkeypatch=monkeypatch)
+    srv.running = False                    # no admissions: only the queue logic
+    a = serving.Request(1, 0, np.zeros((70, 3), dtype=np.int64))
+    b = serving.Request(2, 0, np.zeros((5, 3), dtype=np.int64))
+    c = serving.Request(3, 0, np.zeros((30, 3), dtype=np.int64))
+    for r in (a, b, c):
+        srv.submit(r)
+    assert [(it[0].rid, it[1], it[2]) for it in srv.queues[0]] == [(1, 0, 32), (1, 32, 64), (1, 64, 70),
+                                                                  (2, 0, 5), (3, 0, 30)]
+    assert a._left == 70 and b._left == 5
+    items, cols = srv._take(0)
+    assert [(it[0].rid, it[1]) for it in items] == [(1, 0)] and cols == 32
+    items, cols = srv._take(0)
+    assert [(it[0].rid, it[1]) for it in items] == [(1, 32)] and cols == 32
+    items, cols = srv._take(0)              # 6 + 5 columns fit, the 30 of the next request do not
+    assert [(it[0].rid, it[1]) for it in items] == [(1, 64), (2, 0)] and cols == 11
+    items, cols = srv._take(0)
+    assert [(it[0].rid, it[1]) for it in items] == [(3, 0)] and cols == 30
+    assert srv._take(0) == ([], 0)
