@@ -161,7 +161,8 @@ hz_status hz_factor(hz_handle* h);
  *   opts  NULL for the defaults
  *   info  NULL or array of R entries, one per right-hand side (iters etc. of its column)
  * Errors: HZ_ERR_STATE (not factored), HZ_ERR_ARG, HZ_ERR_ADMISSION (workspace for R
- * does not fit), HZ_ERR_NONFINITE, HZ_ERR_NO_CONVERGENCE (u and info still written).
+ * does not fit), HZ_ERR_OOM, HZ_ERR_NONFINITE, HZ_ERR_NO_CONVERGENCE (u and info still written),
+ * HZ_ERR_TIMEOUT (a tensor-core kernel's bounded wait gave up), HZ_ERR_CUDA.
  */
 hz_status hz_solve(hz_handle* h, const double* rhs, int32_t R, double* u,
                    const hz_solve_opts* opts, hz_solve_info* info);
@@ -199,7 +200,7 @@ hz_status hz_solve_host(hz_handle* h, const double* rhs_host, int32_t R, double*
  * resident factors and problem data (read-only) and gets its own solve workspaces, error flags
  * and stream, so that several solves of the same (model, omega) can run at once (one host
  * thread per handle).  src must stay alive until every handle created from it is destroyed.
- * Errors: HZ_ERR_ARG, HZ_ERR_STATE (src not factored), HZ_ERR_OOM.
+ * Errors: HZ_ERR_ARG, HZ_ERR_STATE (src not factored), HZ_ERR_OOM, HZ_ERR_CUDA.
  */
 hz_status hz_create_shared(hz_handle* src, void* stream, hz_handle** out);
 
