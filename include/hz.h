@@ -92,7 +92,8 @@ typedef struct {
 
 typedef struct hz_handle hz_handle;
 
-/* Fills *opts with the defaults listed above for the given precision. */
+/* Fills *opts with the defaults listed above for the given precision (the Krylov solve of Eq. 15;
+ * the paper's experiments stop GMRES at a relative residual of 1e-7, Numerical Experiments section). */
 void hz_default_opts(hz_precision prec, hz_solve_opts* opts);
 
 /*
@@ -179,14 +180,16 @@ hz_status hz_solve(hz_handle* h, const double* rhs, int32_t R, double* u,
  *   opts      NULL for each member's defaults
  *   info      NULL, or n pointers to arrays of R[i] entries (each may be NULL)
  *   statuses  NULL or n statuses
- * Returns HZ_OK or the first member's failure status.
+ * No counterpart in the paper's algorithms (it solves one problem at a time on a cluster): the
+ * batching of uneven problems the single-GPU design adds.  Returns HZ_OK or the first member's
+ * failure status.
  */
 hz_status hz_solve_group(hz_handle* const* hs, int32_t n, const double* const* rhs, const int32_t* R,
                          double* const* u, const hz_solve_opts* opts, hz_solve_info* const* info,
                          hz_status* statuses);
 
 /*
- * hz_solve_host -- as hz_solve with HOST rhs and u: copies rhs to the device, solves,
+ * hz_solve_host -- as hz_solve (Algorithm 2) with HOST rhs and u: copies rhs to the device, solves,
  * copies u back (end-to-end entry point).  Same errors as hz_solve.  The device copies of the two
  * volumes (2 x R x nx*ny*nz complex128) are kept by the handle for later calls and released by
  * hz_destroy (or replaced when a later call has more right-hand sides); pinned host buffers
@@ -200,16 +203,18 @@ hz_status hz_solve_host(hz_handle* h, const double* rhs_host, int32_t R, double*
  * resident factors and problem data (read-only) and gets its own solve workspaces, error flags
  * and stream, so that several solves of the same (model, omega) can run at once (one host
  * thread per handle).  src must stay alive until every handle created from it is destroyed.
+ * No counterpart in the paper: the factors of Algorithm 1 shared by the serving workers.
  * Errors: HZ_ERR_ARG, HZ_ERR_STATE (src not factored), HZ_ERR_OOM, HZ_ERR_CUDA.
  */
 hz_status hz_create_shared(hz_handle* src, void* stream, hz_handle** out);
 
-/* hz_destroy -- frees every device and host buffer the handle owns (NULL is allowed). */
+/* hz_destroy -- frees every device and host buffer the handle owns (NULL is allowed).  No
+ * counterpart in the paper (resource management). */
 hz_status hz_destroy(hz_handle* h);
 
 /* One-line description of the last failure on this handle ("" if none); the string
  * stays valid until the next call on the handle.  h may be NULL (reports failures of
- * hz_create). */
+ * hz_create and hz_symbolic_shape).  No counterpart in the paper (error reporting). */
 const char* hz_last_error(const hz_handle* h);
 
 /* ------------------------------------------------------------------------------------
@@ -217,18 +222,20 @@ const char* hz_last_error(const hz_handle* h);
  * on the device so that it can be checked on its own; none is needed for a solve.
  * ------------------------------------------------------------------------------------ */
 
-/* Layer geometry: owned global planes [lo, hi] and extended local grid [zlo, zhi]
- * of layer ell (0-based). */
+/* Layer geometry of the layered decomposition (Formulation section, Fig. 1 and Eq. 6): owned
+ * global planes [lo, hi] and extended local grid [zlo, zhi] of layer ell (0-based). */
 hz_status hz_layer_info(const hz_handle* h, int32_t ell, int32_t* lo, int32_t* hi,
                         int32_t* zlo, int32_t* zhi);
 
-/* Statistics of the symbolic/numeric factorization: number of tree nodes, stored
+/* Statistics of the factorization of Algorithm 1 (the multifrontal solver of the Local Solves
+ * section; its cost model is in the Complexity of Polarized Traces section): number of tree nodes, stored
  * factor entries (padded tiles, summed over layers), factorization flops (real),
  * front workspace bytes, and the time hz_factor took in milliseconds. */
 hz_status hz_factor_stats(const hz_handle* h, int64_t* nodes, int64_t* factor_entries,
                           double* factor_flops, int64_t* workspace_bytes, float* factor_ms);
 
-/* Bytes of packed factors streamed by one forward+backward substitution of layer ell
+/* Cost of one local solve (the substitutions of the Local Solves section): bytes of packed
+ * factors streamed by one forward+backward substitution of layer ell
  * (each factor tile read once forward, once backward), and its real flop count per
  * right-hand-side column. */
 hz_status hz_layer_solve_cost(const hz_handle* h, int32_t ell, double* bytes, double* flops_per_col);
@@ -305,13 +312,15 @@ hz_status hz_trace_blocks(hz_handle* h, int32_t max_cols, int64_t* bytes);
  * t device complex [R][K][2][ny][nx]; u device complex [R][nz][ny][nx]. */
 hz_status hz_reconstruct(hz_handle* h, const double* rhs, const double* t, int32_t R, double* u);
 
-/* FP64 volume residual r = S f - A u (7-point stencil of the global operator) and its
- * per-column relative norms ||r|| / ||S f||; r may be NULL. */
+/* FP64 volume residual r = S f - A u of the global discrete system (Formulation section: the
+ * 7-point stencil with the stretched PML) and its per-column relative norms ||r|| / ||S f||; r may
+ * be NULL.  The mixed precision's defect correction uses it; the paper (FP64 throughout) has none. */
 hz_status hz_volume_residual(hz_handle* h, const double* rhs, const double* u, int32_t R,
                              double* r, double* relres_host);
 
 /* ------------------------------------------------------------------------------------
- * Measurement.  hz_profile_begin starts recording CUDA events around every batched
+ * Measurement (no counterpart in the paper, which reports wall-clock times per stage in the
+ * tables of its Numerical Experiments section).  hz_profile_begin starts recording CUDA events around every batched
  * forward+backward substitution (the kernel family that dominates the online phase);
  * hz_profile_end synchronizes the handle's stream and returns the number of recorded
  * substitution calls, their summed device time in ms, and the summed algorithmic factor
@@ -376,20 +385,20 @@ int64_t hz_kernel_launches(void);
 /* Text table of the last detail-profiled interval (hz_profile_begin_detail .. hz_profile_end):
  * one line per kernel kind, substitution phase (FA, FB, BA, BB) and tree level with its launches,
  * work items (tasks, before the split into column chunks), summed device ms and algorithmic
- * TFLOP/s.  The string stays valid until the next call on the handle. */
+ * TFLOP/s.  The string stays valid until the next call on the handle.  No counterpart in the paper. */
 const char* hz_profile_report(hz_handle* h);
 
 /* Per-kernel-kind device time of the last hz_factor on this handle (one line per kind: launch
  * groups timed and summed ms), recorded only when the environment variable HZ_FACTOR_PROFILE=1
  * was set at hz_create ("" otherwise; the event pairs serialise nothing but add host work).  The
- * string stays valid until the next hz_factor on the handle. */
+ * string stays valid until the next hz_factor on the handle.  No counterpart in the paper. */
 const char* hz_factor_report(hz_handle* h);
 
 /* The substitution autotuner's record for this handle: one line per tuned batch signature
  * (layer shapes and column width) with the time of every candidate split-K depth and column
  * chunk and the choice made.  The autotuner runs the first time a signature is solved (set the
  * environment variable HZ_AUTOTUNE=0 before hz_create to keep the fixed defaults).  The string
- * stays valid until the next call on the handle. */
+ * stays valid until the next call on the handle.  No counterpart in the paper. */
 const char* hz_tuning_report(hz_handle* h);
 
 #ifdef __cplusplus
