@@ -16,15 +16,21 @@ Contents
                     direct solve (SuperLU on a nested-dissection-ordered
                     matrix) and a dense LAPACK solve for tiny grids.
 ``polarized``       a slow, step-by-step model of the method itself (layer
-                    decomposition, local solves, the blocks of the polarized
-                    system, the Gauss-Seidel preconditioner, GMRES and the
-                    local reconstruction; Algorithms 1-9), used to pin
+                    decomposition, local solves, the SIE matrix, the blocks of
+                    the polarized system, the Gauss-Seidel preconditioner,
+                    GMRES and the local reconstruction; Algorithms 1-9), and
+                    the explicit trace-to-trace blocks, used to pin
                     intermediate quantities.
+``multifrontal``    the global solve again, organised as a multifrontal
+                    factorization with a generic symbolic phase, for grids too
+                    large for SuperLU (96^3 - 160^3).
 
 Pins (what each function is checked against, in ``tests/test_oracle_*.py``):
 dense LAPACK solve, an independent Kronecker-product assembly, exact complex
 symmetry, discrete reciprocity, residual <= 1e-12, convergence to the free
 space Green's function -exp(ikr)/(4 pi r), exactness of the Green's
 representation formula (Theorem 1 of the 2D polarized-traces paper, cited
-in the SIE section), and the special cases L = 1 and L = 2.
+in the SIE section), the exact traces solving the SIE, the reductive case of
+exact local Green's functions, reciprocity of the explicit trace blocks, and
+the special cases L = 1 and L = 2.
 """
