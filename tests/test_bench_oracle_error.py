@@ -1,4 +1,4 @@
-"""bench.py's accuracy report against stored oracle values (no GPU): the sampled error is exact,
+"""bench.py's accuracy report and clock record (no GPU): the sampled error is exact,
 and the full-grid estimate from seeded complex Gaussian sketches <w_k, u> (E|<w, e>|^2 = ||e||^2)
 recovers a planted error's relative norm, here checked on a synthetic reference file of the same
 format as the stored 128^3 one."""
@@ -42,3 +42,21 @@ def test_samples_and_sketch_estimate(tmp_path, monkeypatch):
     # the reference itself has zero error, and a subset of columns picks the matching rows
     out0 = bench.oracle_error(torch.from_numpy(u_ref[1:]), np.array([1, 2]), "synthetic")
     assert out0["max_rel_err_samples"] < 1e-15 and out0["max_rel_err_full_grid_sketch"] < 1e-12
+
+
+def test_clock_sampler_summary():
+    """The clock record of the timed region: median SM clock under load, the maximum, and every
+    throttle reason seen active (the fields of the nvidia-smi query the bench runs)."""
+    cs = bench.ClockSampler(0)
+    cs.proc = type("P", (), {"terminate": lambda self: None, "wait": lambda self, timeout=None: 0})()
+    cs.lines = [
+        "0, 2070, 2070, 1100.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1900, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "0, 2060, 2070, 1300.0, 0x40, Not Active, Active, Not Active, Not Active",
+    ]
+    out = cs.stop()
+    assert out["sm_mhz"] == 2065.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 4
+    assert out["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    assert bench.ClockSampler(0).stop()["reasons"] == ["nvidia-smi unavailable"]
